@@ -1,0 +1,250 @@
+/*
+ * bodex.h -- C ABI of the GB300 (sm_103a) BODex coarse-stage hot path.
+ *
+ * BODex (arXiv 2412.16490) synthesises dexterous grasps by a bilevel
+ * program (Sec. IV-A, Eqs. (3)-(9)): an upper level does gradient descent
+ * on the hand pose x, and at every iteration each of s lower-level QPs
+ * finds contact forces that best realise a desired wrench.  One upper
+ * iteration of the coarse stage (Secs. IV-B, IV-C) is:
+ *
+ *   forward kinematics -> fingertip contact points c_i
+ *   -> SDF nearest-point query: object point p_i, inward normal n_i
+ *   -> grasp matrix G = [G_1 .. G_m] (Eq. (2))
+ *   -> s QPs  Q_j = min |beta t_j - G y|^2  over the friction pyramids (Eqs. (7)-(9))
+ *   -> energy E = w_Q sum_j Q_j + w_d sum_i (phi_i - alpha - delta)^2
+ *   -> dE/dx (envelope theorem) -> Adam step on x, clamp to limits (Eq. (4)).
+ *
+ * Conventions for every entry point:
+ *   - Return value is a status code (BODEX_OK on success).  No C++
+ *     exception and no process exit crosses this boundary.
+ *     bodex_last_error() returns a message for the calling thread's last
+ *     failure.
+ *   - Array arguments are CALLER-OWNED DEVICE pointers (e.g. PyTorch CUDA
+ *     tensors), contiguous, row-major, float32 unless the comment says
+ *     int32.  The library neither frees nor keeps them after the call.
+ *     Work is enqueued on `stream` (a cudaStream_t passed as void*; NULL is
+ *     the legacy default stream) and is asynchronous.  Launch errors are
+ *     reported by the call; faults during execution surface at the next
+ *     synchronising call (bodex_sync).
+ *   - Descriptor structs (bodex_hand_desc, bodex_object_desc) point to HOST
+ *     memory and are copied during the create call.
+ *   - Handles own their device memory until *_destroy.
+ *   - Per-instance problems (non-finite input, a QP that did not reach the
+ *     residual target, a degenerate SDF normal) are written to the optional
+ *     `status` outputs and do not fail the call.
+ *
+ * Notation: B grasps, m contacts, n revolute joints, D = 6 + n pose
+ * entries, s desired wrenches, nv = 3m QP variables, nc = 9m + 1 QP rows.
+ */
+#ifndef BODEX_H
+#define BODEX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status */
+#define BODEX_OK 0
+#define BODEX_ERR_INVALID 1        /* bad argument (null pointer, size, unsupported shape) */
+#define BODEX_ERR_CUDA 2           /* a CUDA runtime call failed */
+#define BODEX_ERR_OOM 3            /* device allocation failed */
+#define BODEX_ERR_INFEASIBLE 4     /* gamma > m, gamma < 0, or inverted limits */
+#define BODEX_ERR_TIMEOUT 5        /* a bounded device wait gave up */
+#define BODEX_ERR_NOT_CONVERGED 6  /* strict mode only: some QP missed eps_abs */
+
+/* per-instance status bits (status outputs) */
+#define BODEX_ST_NONFINITE 1       /* non-finite input or result */
+#define BODEX_ST_NOT_CONVERGED 2   /* QP residual above eps_abs after max_iter */
+#define BODEX_ST_DEGENERATE_NORMAL 4 /* |grad phi| < 1e-12 at a contact */
+
+/* ---------------------------------------------------------------- limits */
+#define BODEX_MAX_JOINTS 32   /* revolute joints per hand */
+#define BODEX_MAX_CONTACTS 5  /* m in {3, 4, 5} are compiled */
+#define BODEX_MAX_CHAIN 8     /* joints between the root and a contact link */
+
+typedef struct bodex_hand_s* bodex_hand_t;
+typedef struct bodex_object_s* bodex_object_t;
+typedef struct bodex_state_s* bodex_state_t;
+
+/* ---------------------------------------------------------------- hand
+ * Hand kinematic tree under a 6-DoF floating base (Sec. IV-B).  Pose
+ * reading: x = [tx, ty, tz, rx, ry, rz, q_1 .. q_n]; the root frame is
+ * Trans(t) Rx(rx) Ry(ry) Rz(rz).  Joint j's frame is
+ *   T_j = T_parent(j) * offset_j * Rot(axis_j, q_j),
+ * with parent(j) < j or -1 for the root.  Contact i is the centre of the
+ * first fingertip sphere (Sec. IV-C), c_{i,l} in the frame of joint
+ * contact_link[i]; its world position is c_{i,w} = R c_{i,l} + T.
+ */
+typedef struct bodex_hand_desc {
+  int n_joints;                /* n, 1..BODEX_MAX_JOINTS */
+  int n_contacts;              /* m, 3..BODEX_MAX_CONTACTS */
+  const int32_t* parent;       /* [n] */
+  const float* offset;         /* [n,12] row-major 3x4 [R | t], parent -> joint */
+  const float* axis;           /* [n,3] unit axis in the joint frame */
+  const float* qmin;           /* [6+n] lower limits, virtual joints first */
+  const float* qmax;           /* [6+n] upper limits */
+  const int32_t* contact_link; /* [m] */
+  const float* contact_local;  /* [m,3] c_{i,l} */
+  float contact_radius;        /* alpha, sphere radius (m) */
+  int n_tip_samples;           /* S for the refinement epilogue, 0 if unused */
+  const float* tip_samples;    /* [m,S,3] fingertip surface samples, link frame */
+} bodex_hand_desc;
+
+/* Copies the template to the device.  Errors: BODEX_ERR_INVALID for sizes
+ * out of range, a parent index >= its joint, a contact chain longer than
+ * BODEX_MAX_CHAIN; BODEX_ERR_INFEASIBLE when qmin > qmax. */
+int bodex_hand_create(const bodex_hand_desc* desc, bodex_hand_t* out);
+int bodex_hand_destroy(bodex_hand_t hand);
+
+/* ---------------------------------------------------------------- object
+ * The object the nearest-point query runs against (Sec. IV-B): an analytic
+ * sphere (kind 0) or a signed distance field sampled at the nodes of an
+ * N^3 grid (kind 1): node (ix, iy, iz) at origin + h (ix, iy, iz), value
+ * index (iz*N + iy)*N + ix, trilinear between nodes; outside the node box
+ * phi(c) = phi(clamp(c)) + |c - clamp(c)|.  The object frame's origin for
+ * G is the gravity centre (Sec. III): the sphere's centre, or for a grid
+ * the mean position of the nodes with negative value, computed in double
+ * precision at creation.
+ */
+typedef struct bodex_object_desc {
+  int kind;             /* 0 = sphere, 1 = grid */
+  float center[3];      /* sphere */
+  float radius;         /* sphere */
+  int n;                /* grid nodes per axis, >= 2 */
+  float h;              /* grid spacing (m) */
+  float origin[3];      /* grid node (0,0,0) */
+  const float* values;  /* HOST pointer, [n^3] */
+} bodex_object_desc;
+
+/* Uploads the grid on `stream`.  Errors: BODEX_ERR_INVALID, BODEX_ERR_OOM. */
+int bodex_object_create(const bodex_object_desc* desc, void* stream, bodex_object_t* out);
+int bodex_object_destroy(bodex_object_t obj);
+/* Host copy of the gravity centre (object-frame origin). */
+int bodex_object_gravity_centre(bodex_object_t obj, float out[3]);
+
+/* ---------------------------------------------------------------- parameters */
+/* Lower-level QP (Sec. IV-A).  The friction cone of Eq. (1) is replaced by
+ * an inscribed pyramid with 8 edges (1, mu cos(k pi/4), mu sin(k pi/4)) in
+ * the contact's (n, d, e) frame; per contact the rows are
+ *   0 <= f_n <= 1,  cos(phi_k) f_d + sin(phi_k) f_e - mu cos(pi/8) f_n <= 0,
+ *   phi_k = (2k+1) pi/8, k = 0..7,
+ * followed by one row  sum_i f_{i,n} >= gamma.  Solved by ADMM in the
+ * operator-splitting form of Stellato et al. (OSQP, 2020), batched as in
+ * ReLU-QP (Bishop et al., 2024): one explicit K^-1 per grasp shared by its
+ * s wrenches, K = P + sigma I + rho A^T A, P = 2 G^T G. */
+typedef struct bodex_qp_params {
+  float mu;          /* friction coefficient */
+  float beta;        /* desired-wrench scale (Eq. (7)) */
+  float gamma;       /* minimum total normal force (Eq. (9)), 0 <= gamma <= m */
+  float rho;         /* ADMM penalty */
+  float sigma;       /* ADMM proximal weight */
+  float alpha;       /* ADMM relaxation, in (0, 2) */
+  float eps_abs;     /* stop when |A y - z|_inf and |P y + q + A^T lam|_inf <= eps_abs;
+                        0 runs exactly max_iter iterations */
+  float eps_reg;     /* optional eps |y|^2 added to the objective (0 = off) */
+  int max_iter;      /* iteration cap per QP solve */
+  int check_every;   /* residual check period (iterations) */
+  int warm;          /* 1: start from the y/z/lam passed in, 0: from zero */
+  int strict;        /* 1: return BODEX_ERR_NOT_CONVERGED if any QP missed eps_abs
+                        (forces a stream synchronisation) */
+} bodex_qp_params;
+
+/* Energy weights (Sec. IV-C): E = w_q sum_j Q_j + w_d sum_i (phi_i - alpha - delta)^2;
+ * delta is the 1 cm pre-grasp margin of Sec. IV-D in the coarse stage. */
+typedef struct bodex_energy_params {
+  float w_q;
+  float w_d;
+  float delta;
+} bodex_energy_params;
+
+/* Upper-level step: Adam (lr_t for the 3 translations, lr_r for all
+ * angles), then clamp x to [qmin, qmax] (Eq. (4)). */
+typedef struct bodex_step_params {
+  float lr_t, lr_r, b1, b2, adam_eps;
+  bodex_energy_params energy;
+  bodex_qp_params qp;
+} bodex_step_params;
+
+/* ---------------------------------------------------------------- calls */
+
+/* FK + nearest-point query + grasp matrix for B poses (Secs. III, IV-B).
+ *   x     [B,D]     poses
+ *   c_w   [B,m,3]   contact points in the world           (out, may be NULL)
+ *   p     [B,m,3]   nearest object points                   (out, may be NULL)
+ *   n     [B,m,3]   inward unit normals                     (out, may be NULL)
+ *   phi   [B,m]     signed distance of c_w                  (out, may be NULL)
+ *   G     [B,6,3m]  grasp matrix, contact i = columns 3i..3i+2 = (n, d, e),
+ *                   p measured from the gravity centre     (out, may be NULL)
+ *   cell  [B,m,3]   int32 voxel cell of each query (0 for a sphere) (out, may be NULL)
+ *   status [B]      int32 per-grasp status bits             (out, may be NULL)
+ * Errors: BODEX_ERR_INVALID (null handles or x, B < 0), BODEX_ERR_CUDA. */
+int bodex_fk_contacts(bodex_hand_t hand, bodex_object_t obj, const float* x, int B, float* c_w, float* p,
+                      float* n, float* phi, float* G, int32_t* cell, int32_t* status, void* stream);
+
+/* Batched lower-level QPs (Sec. IV-A, Eqs. (7)-(9)) for B grasps x s wrenches.
+ *   G      [B,6,3m]     grasp matrices
+ *   T      [s,6]        desired unit wrenches t_j
+ *   y      [B,s,3m]     forces (in: warm start when params->warm, out: solution)
+ *   z      [B,s,9m+1]   ADMM constraint copy (in/out, same rule)
+ *   lam    [B,s,9m+1]   ADMM multipliers (in/out, same rule)
+ *   Q      [B,s]        |beta t_j - G y_j|^2 at the returned y (out)
+ *   iters  [B,s]        int32 iterations used (out, may be NULL)
+ *   status [B,s]        int32 status bits (out, may be NULL)
+ *   res    [B,s,2]      final (primal, dual) inf-norm residuals (out, may be NULL)
+ * m must be 3, 4 or 5; s in 1..16.  Errors: BODEX_ERR_INVALID,
+ * BODEX_ERR_INFEASIBLE (gamma outside [0, m]), BODEX_ERR_CUDA,
+ * BODEX_ERR_NOT_CONVERGED (strict mode). */
+int bodex_qp_solve_batch(const float* G, int B, int m, const float* T, int s, const bodex_qp_params* params,
+                         float* y, float* z, float* lam, float* Q, int32_t* iters, int32_t* status, float* res,
+                         void* stream);
+
+/* Optimiser state for B grasps and s wrenches: pose x [B,D], Adam moments
+ * [B,D], step counter, and the ADMM warm start of every QP.  Owns its
+ * device memory.  Errors: BODEX_ERR_INVALID, BODEX_ERR_OOM. */
+int bodex_state_create(bodex_hand_t hand, int B, int s, bodex_state_t* out);
+int bodex_state_destroy(bodex_state_t state);
+/* Sets the pose from a device array [B,D] and resets Adam, the step
+ * counter and the ADMM warm start.  Asynchronous on `stream`. */
+int bodex_state_set_pose(bodex_state_t state, const float* x, void* stream);
+/* Copies the pose to a device array [B,D]. */
+int bodex_state_get_pose(bodex_state_t state, float* x, void* stream);
+/* Copies the Adam moments m, v [B,D] (either may be NULL) and returns the step count. */
+int bodex_state_get_adam(bodex_state_t state, float* m, float* v, int* step, void* stream);
+
+/* Energy and gradient at B poses: E [B], dE/dx [B,D] (envelope theorem,
+ * Sec. IV-A: the feasible set of the QPs does not depend on x, so
+ * dQ_j/dG = -2 r_j y_j^T with r_j = beta t_j - G y_j).
+ *   T      [s,6] desired wrenches
+ *   warm   optional state whose ADMM warm start is used and updated
+ *          (must have been created for the same B and s), or NULL
+ *   E      [B]   (out)      dEdx [B,D] (out, may be NULL)
+ *   Q      [B,s] (out, may be NULL)   y [B,s,3m] (out, may be NULL)
+ *   status [B]   int32 (out, may be NULL)
+ * Errors: BODEX_ERR_INVALID, BODEX_ERR_INFEASIBLE, BODEX_ERR_CUDA. */
+int bodex_energy_grad(bodex_hand_t hand, bodex_object_t obj, const float* x, int B, const float* T, int s,
+                      const bodex_step_params* params, bodex_state_t warm, float* E, float* dEdx, float* Q,
+                      float* y, int32_t* status, void* stream);
+
+/* n_steps upper-level iterations on the state, fused into one kernel launch:
+ * each iteration evaluates E and dE/dx at the current pose (ADMM warm
+ * started from the previous iteration, params->qp.max_iter iterations),
+ * takes an Adam step and clamps.  E_last [B] (may be NULL) receives E at
+ * the last evaluated pose; status [B] (may be NULL) ORs the per-grasp bits.
+ * Errors: BODEX_ERR_INVALID, BODEX_ERR_INFEASIBLE, BODEX_ERR_CUDA. */
+int bodex_step(bodex_hand_t hand, bodex_object_t obj, bodex_state_t state, const float* T, int s, int n_steps,
+               const bodex_step_params* params, float* E_last, int32_t* status, void* stream);
+
+/* Blocks until `stream` is idle; BODEX_ERR_CUDA if a fault occurred. */
+int bodex_sync(void* stream);
+/* Message for the calling thread's last non-OK status ("" if none). */
+const char* bodex_last_error(void);
+/* Library version string. */
+const char* bodex_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BODEX_H */

@@ -1,0 +1,916 @@
+// BODex coarse-stage hot path for GB300 (sm_103a): kernels and the C ABI
+// declared in include/bodex.h.
+//
+// Kernel layout.  One CTA holds GPB grasps and s lanes (threads) per grasp,
+// GPB * s = 96 threads for s = 6 or 12.  Lane j of a grasp owns the QP of
+// desired wrench t_j and keeps its ADMM iterate (y: 3m, w: 9m+1 floats) in
+// registers; the grasp's G and explicit K^-1 sit in shared memory and are
+// read by all of its lanes.  Lanes 0..m-1 also own one contact each for the
+// kinematics, the SDF query and the adjoint.  The fused step kernel runs
+// every upper iteration of a launch back to back without leaving the CTA:
+// pose, Adam moments and warm starts never return to HBM between steps.
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/bodex.h"
+#include "bodex_device.cuh"
+
+using namespace bodex;
+
+// ============================================================================ error state
+namespace {
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* where) {
+  return fail(BODEX_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+#define BODEX_CUDA(call)                                    \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+  } while (0)
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+}  // namespace
+
+struct bodex_hand_s {
+  HandDev host;
+  HandDev* dev = nullptr;
+};
+struct bodex_object_s {
+  ObjDev dev;
+  float* grid = nullptr;
+};
+struct bodex_state_s {
+  int B = 0, s = 0, m = 0, D = 0;
+  float* x = nullptr;
+  float* am = nullptr;
+  float* av = nullptr;
+  float* qy = nullptr;  // [B, s, 3m]
+  float* qw = nullptr;  // [B, s, 9m+1]
+  int t = 0;
+};
+
+// ============================================================================ shared-memory layout
+constexpr int CTA_LANES = 96;
+
+__host__ __device__ constexpr int align4(int v) { return (v + 3) & ~3; }
+
+template <int M>
+struct Lay {
+  static constexpr int NV = 3 * M, NC = 9 * M + 1, NVP = (NV + 3) & ~3;
+  // K^-1 block per grasp; the stride is skewed (== 20 mod 32 words) so that
+  // lanes of two or three grasps in one warp hit disjoint banks.
+  static constexpr int KS = NV * NVP + ((20 - (NV * NVP) % 32) + 32) % 32;
+  static constexpr int CTW = 24;  // floats per contact record
+  static constexpr int oG = 0;
+  static constexpr int oK = oG + 6 * NV;
+  static constexpr int oCT = oK + NV * NV;
+  static constexpr int oRY = oCT + CTW * M;
+  static constexpr int oQ = oRY + SMAX * (6 + NV);
+  static constexpr int oDG = oQ + SMAX;
+  static constexpr int oCB = oDG + 6 * NV;
+  static constexpr int oX = oCB + M * (6 + MAXCHAIN);
+  static constexpr int oAM = oX + MAXD;
+  static constexpr int oAV = oAM + MAXD;
+  static constexpr int oSC = oAV + MAXD;
+  static constexpr int PER = align4(oSC + 4);
+  static constexpr int HAND_WORDS = align4((int)(sizeof(HandDev) / 4));
+  static size_t bytes(int gpb) { return 4u * (size_t)(HAND_WORDS + gpb * (KS + PER)); }
+};
+
+// Contact record in shared memory: c(3) p(3) n(3) phi g(3) h(6) cell(3) degenerate.
+__device__ __forceinline__ void store_ct(float* r, const ContactGeo& k) {
+  for (int a = 0; a < 3; ++a) {
+    r[a] = k.c[a];
+    r[3 + a] = k.p[a];
+    r[6 + a] = k.n[a];
+    r[10 + a] = k.g[a];
+    r[19 + a] = __int_as_float(k.cell[a]);
+  }
+  r[9] = k.phi;
+  for (int e = 0; e < 6; ++e) r[13 + e] = k.h[e];
+  r[22] = __int_as_float(k.degenerate);
+}
+__device__ __forceinline__ ContactGeo load_ct(const float* r) {
+  ContactGeo k;
+  for (int a = 0; a < 3; ++a) {
+    k.c[a] = r[a];
+    k.p[a] = r[3 + a];
+    k.n[a] = r[6 + a];
+    k.g[a] = r[10 + a];
+    k.cell[a] = __float_as_int(r[19 + a]);
+  }
+  k.phi = r[9];
+  for (int e = 0; e < 6; ++e) k.h[e] = r[13 + e];
+  k.degenerate = __float_as_int(r[22]);
+  return k;
+}
+
+__device__ __forceinline__ void copy_hand_to_smem(const HandDev* src, float* dst) {
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(dst);
+  const int words = (int)(sizeof(HandDev) / 4);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = __ldg(s + i);
+}
+
+__device__ __forceinline__ bool finite3(const float* v) {
+  return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
+}
+
+// ============================================================================ kernel: FK + contacts + G
+template <int M>
+__global__ void __launch_bounds__(128) fk_contacts_kernel(const HandDev* __restrict__ hand, ObjDev obj,
+                                                          const float* __restrict__ x, int B, float* c_w,
+                                                          float* p_out, float* n_out, float* phi_out, float* G_out,
+                                                          int32_t* cell_out, int32_t* status_out) {
+  __shared__ __align__(16) float hs[Lay<M>::HAND_WORDS];
+  copy_hand_to_smem(hand, hs);
+  __syncthreads();
+  const HandDev& H = *reinterpret_cast<const HandDev*>(hs);
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  constexpr int NV = 3 * M;
+  const int D = H.D;
+  float xl[MAXD];
+  int st = 0;
+  for (int k = 0; k < D; ++k) {
+    xl[k] = x[(size_t)b * D + k];
+    if (!isfinite(xl[k])) st |= BODEX_ST_NONFINITE;
+  }
+  float Gl[6 * NV];
+  for (int i = 0; i < M; ++i) {
+    float c[3];
+    fk_contact(H, i, xl, c, nullptr);
+    const ContactGeo k = contact_geometry(obj, c);
+    if (k.degenerate) st |= BODEX_ST_DEGENERATE_NORMAL;
+    if (!finite3(k.p) || !finite3(k.n) || !isfinite(k.phi)) st |= BODEX_ST_NONFINITE;
+    write_G_block(k, i, NV, Gl);
+    const size_t o = ((size_t)b * M + i) * 3;
+    const float gc[3] = {obj.gcx, obj.gcy, obj.gcz};
+    for (int a = 0; a < 3; ++a) {
+      if (c_w) c_w[o + a] = k.c[a];
+      if (p_out) p_out[o + a] = k.p[a] + gc[a];
+      if (n_out) n_out[o + a] = k.n[a];
+      if (cell_out) cell_out[o + a] = k.cell[a];
+    }
+    if (phi_out) phi_out[(size_t)b * M + i] = k.phi;
+  }
+  if (G_out)
+    for (int e = 0; e < 6 * NV; ++e) G_out[(size_t)b * 6 * NV + e] = Gl[e];
+  if (status_out) status_out[b] = st;
+}
+
+// ============================================================================ per-grasp QP setup (shared by kernels)
+// Lane 0 builds K and factors it; then the grasp's lanes write the columns
+// of K^-1.  Must be called by every thread of the CTA (contains barriers).
+template <int M>
+__device__ inline void setup_kinv(bool active, int lane, int S, float* Gs, float* Ks, float* Kinv,
+                                  const AdmmCfg& cfg, int* stat) {
+  constexpr int NV = 3 * M;
+  if (active && lane == 0) {
+    build_K<M>(Gs, cfg, Ks);
+    if (!cholesky<NV>(Ks)) atomicOr(stat, BODEX_ST_NONFINITE);
+  }
+  __syncthreads();
+  if (active)
+    for (int col = lane; col < NV; col += S) chol_inverse_column<NV>(Ks, col, Kinv, Lay<M>::NVP);
+  __syncthreads();
+}
+
+// ============================================================================ kernel: batched QP
+template <int M>
+__global__ void __launch_bounds__(CTA_LANES) qp_solve_kernel(const float* __restrict__ Gin, int B,
+                                                             const float* __restrict__ T, int S, AdmmCfg cfg,
+                                                             int warm, float* yio, float* zio, float* lio,
+                                                             float* Qout, int32_t* iters_out, int32_t* status_out,
+                                                             float* res_out) {
+  using L = Lay<M>;
+  constexpr int NV = L::NV, NC = L::NC;
+  extern __shared__ __align__(16) float smem[];
+  const int GPB = blockDim.x / S;
+  const int gl = threadIdx.x / S, lane = threadIdx.x % S;
+  const int b = blockIdx.x * GPB + gl;
+  const bool active = (gl < GPB) && (b < B);
+  float* kin = smem + L::HAND_WORDS + gl * L::KS;
+  float* per = smem + L::HAND_WORDS + GPB * L::KS + gl * L::PER;
+  float* Gs = per + L::oG;
+  int* stat = reinterpret_cast<int*>(per + L::oSC + 1);
+  if (active) {
+    for (int e = lane; e < 6 * NV; e += S) Gs[e] = Gin[(size_t)b * 6 * NV + e];
+    if (lane == 0) *stat = 0;
+  }
+  __syncthreads();
+  setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg, stat);
+  if (!active) return;  // no barriers below
+  const size_t q = (size_t)b * S + lane;
+  float y[NV], w[NC], mq[NV];
+  float t[6];
+  for (int r = 0; r < 6; ++r) t[r] = T[lane * 6 + r];
+  neg_q<M>(Gs, t, cfg.beta, mq);
+  if (warm) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) y[a] = yio[q * NV + a];
+#pragma unroll
+    for (int r = 0; r < NC; ++r) w[r] = zio[q * NC + r] + lio[q * NC + r] / cfg.rho;
+  } else {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) y[a] = 0.f;
+#pragma unroll
+    for (int r = 0; r < NC; ++r) w[r] = 0.f;
+  }
+  float rp, rd;
+  bool conv;
+  const int it = admm_solve<M>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
+  float Q = 0.f;
+  bool fin = true;
+#pragma unroll
+  for (int r = 0; r < 6; ++r) {
+    float s = cfg.beta * t[r];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) s = fmaf(-Gs[r * NV + a], y[a], s);
+    Q = fmaf(s, s, Q);
+  }
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    yio[q * NV + a] = y[a];
+    fin = fin && isfinite(y[a]);
+  }
+#pragma unroll
+  for (int r = 0; r < NC; ++r) {
+    const float p = proj_row<M>(w[r], r, cfg.gamma);
+    zio[q * NC + r] = p;
+    lio[q * NC + r] = cfg.rho * (w[r] - p);
+  }
+  Qout[q] = Q;
+  if (iters_out) iters_out[q] = it;
+  if (res_out) {
+    res_out[2 * q] = rp;
+    res_out[2 * q + 1] = rd;
+  }
+  int st = *stat;
+  if (!fin || !isfinite(Q)) st |= BODEX_ST_NONFINITE;
+  if (cfg.eps > 0.f && !conv) st |= BODEX_ST_NOT_CONVERGED;
+  if (status_out) status_out[q] = st;
+}
+
+// ============================================================================ kernel: fused evaluation / step
+struct FusedArgs {
+  const HandDev* hand;
+  ObjDev obj;
+  const float* T;
+  int S, B;
+  AdmmCfg cfg;
+  float w_q, w_d, delta;
+  float lr_t, lr_r, b1, b2, adam_eps;
+  int n_steps, t0;
+  // pose input (eval) or state pose (step), updated in place for step
+  const float* x_in;
+  float* x_state;
+  float* am;
+  float* av;
+  float* qy;  // warm start, may be null (eval: cold start)
+  float* qw;
+  // outputs
+  float* E;
+  float* dEdx;
+  float* Qout;
+  float* yout;
+  int32_t* status;
+};
+
+enum { MODE_EVAL = 0, MODE_STEP = 1 };
+
+template <int M, int MODE>
+__global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
+  using L = Lay<M>;
+  constexpr int NV = L::NV, NC = L::NC;
+  extern __shared__ __align__(16) float smem[];
+  copy_hand_to_smem(A.hand, smem);
+  const int S = A.S;
+  const int GPB = blockDim.x / S;
+  const int gl = threadIdx.x / S, lane = threadIdx.x % S;
+  const int b = blockIdx.x * GPB + gl;
+  const bool active = (gl < GPB) && (b < A.B);
+  const HandDev& H = *reinterpret_cast<const HandDev*>(smem);
+  float* kin = smem + L::HAND_WORDS + gl * L::KS;
+  float* per = smem + L::HAND_WORDS + GPB * L::KS + gl * L::PER;
+  float* Gs = per + L::oG;
+  float* xs = per + L::oX;
+  float* ams = per + L::oAM;
+  float* avs = per + L::oAV;
+  float* sc = per + L::oSC;
+  int* stat = reinterpret_cast<int*>(sc + 1);
+  __syncthreads();  // hand copied
+  const int D = H.D;
+  const AdmmCfg& cfg = A.cfg;
+
+  if (active) {
+    const float* xsrc = (MODE == MODE_STEP) ? A.x_state : A.x_in;
+    for (int k = lane; k < D; k += S) {
+      xs[k] = xsrc[(size_t)b * D + k];
+      if (MODE == MODE_STEP) {
+        ams[k] = A.am[(size_t)b * D + k];
+        avs[k] = A.av[(size_t)b * D + k];
+      }
+    }
+    if (lane == 0) *stat = 0;
+  }
+  // ADMM warm start of this lane's QP, kept in registers across steps
+  float y[NV], w[NC];
+  const size_t q = (size_t)b * S + lane;
+  if (active && A.qy) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) y[a] = A.qy[q * NV + a];
+#pragma unroll
+    for (int r = 0; r < NC; ++r) w[r] = A.qw[q * NC + r];
+  } else {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) y[a] = 0.f;
+#pragma unroll
+    for (int r = 0; r < NC; ++r) w[r] = 0.f;
+  }
+  float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (active)
+    for (int r = 0; r < 6; ++r) t[r] = A.T[lane * 6 + r];
+  __syncthreads();
+
+  for (int step = 0; step < A.n_steps; ++step) {
+    // ---- A1-A3: kinematics, nearest-point query, grasp matrix (lane = contact)
+    if (active && lane < M) {
+      float c[3];
+      fk_contact(H, lane, xs, c, nullptr);
+      const ContactGeo k = contact_geometry(A.obj, c);
+      store_ct(per + L::oCT + L::CTW * lane, k);
+      write_G_block(k, lane, NV, Gs);
+      int st = 0;
+      if (k.degenerate) st |= BODEX_ST_DEGENERATE_NORMAL;
+      if (!finite3(k.p) || !finite3(k.n) || !isfinite(k.phi)) st |= BODEX_ST_NONFINITE;
+      if (st) atomicOr(stat, st);
+    }
+    __syncthreads();
+    // ---- A4: K^-1 per grasp
+    setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg, stat);
+    // ---- A5: ADMM, one QP per lane
+    if (active) {
+      float mq[NV];
+      neg_q<M>(Gs, t, cfg.beta, mq);
+      float rp, rd;
+      bool conv;
+      admm_solve<M>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
+      float* ry = per + L::oRY + lane * (6 + NV);
+      float Q = 0.f;
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        float s = cfg.beta * t[r];
+#pragma unroll
+        for (int a = 0; a < NV; ++a) s = fmaf(-Gs[r * NV + a], y[a], s);
+        ry[r] = s;
+        Q = fmaf(s, s, Q);
+      }
+#pragma unroll
+      for (int a = 0; a < NV; ++a) ry[6 + a] = y[a];
+      per[L::oQ + lane] = Q;
+      int st = 0;
+      if (cfg.eps > 0.f && !conv) st |= BODEX_ST_NOT_CONVERGED;
+      if (!isfinite(Q)) st |= BODEX_ST_NONFINITE;
+      if (st) atomicOr(stat, st);
+    }
+    __syncthreads();
+    // ---- A6: energy;  A7 (part 1): dE/dG = -2 w_Q sum_j r_j y_j^T
+    if (active) {
+      const float* ry = per + L::oRY;
+      for (int e = lane; e < 6 * NV; e += S) {
+        const int r = e / NV, a = e % NV;
+        float s = 0.f;
+        for (int j = 0; j < S; ++j) s = fmaf(ry[j * (6 + NV) + r], ry[j * (6 + NV) + 6 + a], s);
+        per[L::oDG + e] = -2.f * A.w_q * s;
+      }
+      if (lane == 0) {
+        float EQ = 0.f;
+        for (int j = 0; j < S; ++j) EQ += per[L::oQ + j];
+        float Ed = 0.f;
+        for (int i = 0; i < M; ++i) {
+          const float r = per[L::oCT + L::CTW * i + 9] - H.alpha - A.delta;
+          Ed = fmaf(r, r, Ed);
+        }
+        sc[0] = A.w_q * EQ + A.w_d * Ed;
+      }
+    }
+    __syncthreads();
+    // ---- A7 (part 2): through the contact geometry and the kinematic chain
+    if (active && lane < M) {
+      const ContactGeo k = load_ct(per + L::oCT + L::CTW * lane);
+      float cols[18];
+      for (int r = 0; r < 6; ++r)
+        for (int cc = 0; cc < 3; ++cc) cols[r * 3 + cc] = per[L::oDG + r * NV + 3 * lane + cc];
+      float dEdc[3];
+      contact_adjoint(k, cols, 2.f * A.w_d * (k.phi - H.alpha - A.delta), dEdc);
+      float jw[6 * MAXCHAIN];
+      float c[3];
+      fk_contact(H, lane, xs, c, jw);
+      float* cb = per + L::oCB + lane * (6 + MAXCHAIN);
+      cb[0] = dEdc[0];
+      cb[1] = dEdc[1];
+      cb[2] = dEdc[2];
+      // root rotations rx, ry, rz: axes through t
+      {
+        float s1, c1, s2, c2;
+        sincosf(xs[3], &s1, &c1);
+        sincosf(xs[4], &s2, &c2);
+        const float om[3][3] = {{1.f, 0.f, 0.f}, {0.f, c1, s1}, {s2, -s1 * c2, c1 * c2}};
+        const float rel[3] = {c[0] - xs[0], c[1] - xs[1], c[2] - xs[2]};
+        for (int k3 = 0; k3 < 3; ++k3) {
+          float v[3];
+          cross3(om[k3], rel, v);
+          cb[3 + k3] = dEdc[0] * v[0] + dEdc[1] * v[1] + dEdc[2] * v[2];
+        }
+      }
+      const int Lc = H.chain_len[lane];
+      for (int kk = 0; kk < Lc; ++kk) {
+        const float rel[3] = {c[0] - jw[6 * kk + 3], c[1] - jw[6 * kk + 4], c[2] - jw[6 * kk + 5]};
+        float v[3];
+        cross3(jw + 6 * kk, rel, v);
+        cb[6 + kk] = dEdc[0] * v[0] + dEdc[1] * v[1] + dEdc[2] * v[2];
+      }
+    }
+    __syncthreads();
+    // ---- gradient assembly (fixed order over contacts) and A8: Adam + clamp
+    if (active) {
+      const float* cb = per + L::oCB;
+      const int tstep = A.t0 + step + 1;
+      const float c1 = 1.f - powf(A.b1, (float)tstep), c2 = 1.f - powf(A.b2, (float)tstep);
+      for (int k = lane; k < D; k += S) {
+        float g = 0.f;
+        if (k < 6) {
+          for (int i = 0; i < M; ++i) g += cb[i * (6 + MAXCHAIN) + k];
+        } else {
+          for (int i = 0; i < M; ++i) {
+            const int pos = H.jpos[i][k - 6];
+            if (pos >= 0) g += cb[i * (6 + MAXCHAIN) + 6 + pos];
+          }
+        }
+        if (MODE == MODE_EVAL) {
+          if (A.dEdx) A.dEdx[(size_t)b * D + k] = g;
+        } else {
+          const float mm = fmaf(A.b1, ams[k], (1.f - A.b1) * g);
+          const float vv = fmaf(A.b2, avs[k], (1.f - A.b2) * g * g);
+          ams[k] = mm;
+          avs[k] = vv;
+          const float lr = k < 3 ? A.lr_t : A.lr_r;
+          const float xn = xs[k] - lr * (mm / c1) / (sqrtf(vv / c2) + A.adam_eps);
+          xs[k] = fminf(fmaxf(xn, H.qmin[k]), H.qmax[k]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- write back
+  if (!active) return;
+  if (lane == 0) {
+    if (A.E) A.E[b] = sc[0];
+    if (A.status) A.status[b] = *stat;
+  }
+  if (MODE == MODE_STEP) {
+    for (int k = lane; k < D; k += S) {
+      A.x_state[(size_t)b * D + k] = xs[k];
+      A.am[(size_t)b * D + k] = ams[k];
+      A.av[(size_t)b * D + k] = avs[k];
+    }
+  }
+  if (A.qy) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) A.qy[q * NV + a] = y[a];
+#pragma unroll
+    for (int r = 0; r < NC; ++r) A.qw[q * NC + r] = w[r];
+  }
+  if (MODE == MODE_EVAL) {
+    if (A.Qout) A.Qout[q] = per[L::oQ + lane];
+    if (A.yout)
+#pragma unroll
+      for (int a = 0; a < NV; ++a) A.yout[q * NV + a] = y[a];
+  }
+}
+
+// ============================================================================ host helpers
+namespace {
+
+int gpb_for(int s) { return std::max(1, CTA_LANES / s); }
+
+template <class K>
+int ensure_smem(K kernel, size_t bytes) {
+  if (bytes > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  }
+  return BODEX_OK;
+}
+
+int check_qp_params(const bodex_qp_params* p, int m) {
+  if (!p) return fail(BODEX_ERR_INVALID, "null qp params");
+  if (!(p->gamma >= 0.f) || p->gamma > (float)m)
+    return fail(BODEX_ERR_INFEASIBLE, "gamma must lie in [0, m]");
+  if (!(p->rho > 0.f) || !(p->sigma >= 0.f) || !(p->alpha > 0.f && p->alpha < 2.f) || p->max_iter < 0 ||
+      !(p->mu >= 0.f))
+    return fail(BODEX_ERR_INVALID, "invalid ADMM parameters");
+  return BODEX_OK;
+}
+
+int launch_err(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return BODEX_OK;
+}
+
+template <int M>
+int run_fused(int mode, const FusedArgs& A, cudaStream_t st) {
+  const int gpb = gpb_for(A.S);
+  const size_t bytes = Lay<M>::bytes(gpb);
+  const dim3 grid((A.B + gpb - 1) / gpb), block(gpb * A.S);
+  if (A.B == 0) return BODEX_OK;
+  if (mode == MODE_STEP) {
+    if (int r = ensure_smem(fused_kernel<M, MODE_STEP>, bytes)) return r;
+    fused_kernel<M, MODE_STEP><<<grid, block, bytes, st>>>(A);
+  } else {
+    if (int r = ensure_smem(fused_kernel<M, MODE_EVAL>, bytes)) return r;
+    fused_kernel<M, MODE_EVAL><<<grid, block, bytes, st>>>(A);
+  }
+  return launch_err("fused_kernel launch");
+}
+
+int dispatch_fused(int m, int mode, const FusedArgs& A, cudaStream_t st) {
+  switch (m) {
+    case 3: return run_fused<3>(mode, A, st);
+    case 4: return run_fused<4>(mode, A, st);
+    case 5: return run_fused<5>(mode, A, st);
+    default: return fail(BODEX_ERR_INVALID, "m must be 3, 4 or 5");
+  }
+}
+
+template <int M>
+int run_qp(const float* G, int B, const float* T, int s, const AdmmCfg& cfg, int warm, float* y, float* z,
+           float* lam, float* Q, int32_t* iters, int32_t* status, float* res, cudaStream_t st) {
+  if (B == 0) return BODEX_OK;
+  const int gpb = gpb_for(s);
+  const size_t bytes = Lay<M>::bytes(gpb);
+  if (int r = ensure_smem(qp_solve_kernel<M>, bytes)) return r;
+  qp_solve_kernel<M><<<(B + gpb - 1) / gpb, gpb * s, bytes, st>>>(G, B, T, s, cfg, warm, y, z, lam, Q, iters,
+                                                                  status, res);
+  return launch_err("qp_solve_kernel launch");
+}
+
+template <int M>
+int run_fk(const bodex_hand_s* h, const bodex_object_s* o, const float* x, int B, float* c_w, float* p, float* n,
+           float* phi, float* G, int32_t* cell, int32_t* status, cudaStream_t st) {
+  if (B == 0) return BODEX_OK;
+  fk_contacts_kernel<M><<<(B + 127) / 128, 128, 0, st>>>(h->dev, o->dev, x, B, c_w, p, n, phi, G, cell, status);
+  return launch_err("fk_contacts_kernel launch");
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+extern "C" {
+
+const char* bodex_last_error(void) { return g_err.c_str(); }
+const char* bodex_version(void) { return "bodex-gb300 0.1 (sm_103a)"; }
+
+int bodex_sync(void* stream) {
+  BODEX_CUDA(cudaStreamSynchronize(as_stream(stream)));
+  return BODEX_OK;
+}
+
+int bodex_hand_create(const bodex_hand_desc* d, bodex_hand_t* out) {
+  if (!d || !out) return fail(BODEX_ERR_INVALID, "null argument");
+  *out = nullptr;
+  const int n = d->n_joints, m = d->n_contacts;
+  if (n < 1 || n > MAXJ) return fail(BODEX_ERR_INVALID, "n_joints out of range");
+  if (m < 3 || m > MAXM) return fail(BODEX_ERR_INVALID, "n_contacts must be 3..5");
+  if (!d->parent || !d->offset || !d->axis || !d->qmin || !d->qmax || !d->contact_link || !d->contact_local)
+    return fail(BODEX_ERR_INVALID, "null array in hand descriptor");
+  HandDev H;
+  std::memset(&H, 0, sizeof(H));
+  H.n = n;
+  H.m = m;
+  H.D = 6 + n;
+  H.alpha = d->contact_radius;
+  H.S = d->n_tip_samples;
+  for (int j = 0; j < n; ++j) {
+    H.parent[j] = d->parent[j];
+    if (H.parent[j] >= j || H.parent[j] < -1) return fail(BODEX_ERR_INVALID, "parent[j] must be -1 or < j");
+    for (int e = 0; e < 12; ++e) H.offset[j][e] = d->offset[12 * j + e];
+    for (int e = 0; e < 3; ++e) H.axis[j][e] = d->axis[3 * j + e];
+  }
+  for (int k = 0; k < 6 + n; ++k) {
+    H.qmin[k] = d->qmin[k];
+    H.qmax[k] = d->qmax[k];
+    if (!(H.qmin[k] <= H.qmax[k])) return fail(BODEX_ERR_INFEASIBLE, "qmin > qmax");
+  }
+  for (int i = 0; i < MAXM; ++i)
+    for (int j = 0; j < MAXJ; ++j) H.jpos[i][j] = -1;
+  for (int i = 0; i < m; ++i) {
+    H.clink[i] = d->contact_link[i];
+    if (H.clink[i] < 0 || H.clink[i] >= n) return fail(BODEX_ERR_INVALID, "contact_link out of range");
+    for (int a = 0; a < 3; ++a) H.clocal[i][a] = d->contact_local[3 * i + a];
+    int chain[MAXJ], L = 0;
+    for (int j = H.clink[i]; j >= 0; j = H.parent[j]) chain[L++] = j;
+    if (L > MAXCHAIN) return fail(BODEX_ERR_INVALID, "contact chain longer than BODEX_MAX_CHAIN");
+    H.chain_len[i] = L;
+    for (int k = 0; k < L; ++k) {
+      H.chain[i][k] = chain[L - 1 - k];
+      H.jpos[i][chain[L - 1 - k]] = (int8_t)k;
+    }
+  }
+  bodex_hand_s* h = new bodex_hand_s();
+  h->host = H;
+  cudaError_t e = cudaMalloc(&h->dev, sizeof(HandDev));
+  if (e != cudaSuccess) {
+    delete h;
+    return fail(BODEX_ERR_OOM, "cudaMalloc hand");
+  }
+  e = cudaMemcpy(h->dev, &h->host, sizeof(HandDev), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(h->dev);
+    delete h;
+    return cuda_fail(e, "cudaMemcpy hand");
+  }
+  *out = h;
+  return BODEX_OK;
+}
+
+int bodex_hand_destroy(bodex_hand_t h) {
+  if (!h) return BODEX_OK;
+  cudaFree(h->dev);
+  delete h;
+  return BODEX_OK;
+}
+
+int bodex_object_create(const bodex_object_desc* d, void* stream, bodex_object_t* out) {
+  if (!d || !out) return fail(BODEX_ERR_INVALID, "null argument");
+  *out = nullptr;
+  bodex_object_s* o = new bodex_object_s();
+  std::memset(&o->dev, 0, sizeof(ObjDev));
+  if (d->kind == 0) {
+    if (!(d->radius > 0.f)) {
+      delete o;
+      return fail(BODEX_ERR_INVALID, "sphere radius must be > 0");
+    }
+    o->dev.kind = 0;
+    o->dev.cx = d->center[0];
+    o->dev.cy = d->center[1];
+    o->dev.cz = d->center[2];
+    o->dev.r = d->radius;
+    o->dev.gcx = d->center[0];
+    o->dev.gcy = d->center[1];
+    o->dev.gcz = d->center[2];
+  } else if (d->kind == 1) {
+    const int N = d->n;
+    if (N < 2 || !(d->h > 0.f) || !d->values) {
+      delete o;
+      return fail(BODEX_ERR_INVALID, "grid needs n >= 2, h > 0 and values");
+    }
+    const size_t cnt = (size_t)N * N * N;
+    o->dev.kind = 1;
+    o->dev.N = N;
+    o->dev.h = d->h;
+    o->dev.inv_h = 1.0f / d->h;
+    o->dev.ox = d->origin[0];
+    o->dev.oy = d->origin[1];
+    o->dev.oz = d->origin[2];
+    // gravity centre: mean of the node positions inside the object (double)
+    double sx = 0, sy = 0, sz = 0;
+    long long inside = 0;
+    for (int iz = 0; iz < N; ++iz)
+      for (int iy = 0; iy < N; ++iy)
+        for (int ix = 0; ix < N; ++ix)
+          if (d->values[((size_t)iz * N + iy) * N + ix] < 0.f) {
+            sx += (double)d->origin[0] + (double)d->h * ix;
+            sy += (double)d->origin[1] + (double)d->h * iy;
+            sz += (double)d->origin[2] + (double)d->h * iz;
+            ++inside;
+          }
+    if (inside > 0) {
+      o->dev.gcx = (float)(sx / inside);
+      o->dev.gcy = (float)(sy / inside);
+      o->dev.gcz = (float)(sz / inside);
+    } else {
+      const double half = 0.5 * (double)d->h * (N - 1);
+      o->dev.gcx = (float)(d->origin[0] + half);
+      o->dev.gcy = (float)(d->origin[1] + half);
+      o->dev.gcz = (float)(d->origin[2] + half);
+    }
+    cudaError_t e = cudaMalloc(&o->grid, cnt * sizeof(float));
+    if (e != cudaSuccess) {
+      delete o;
+      return fail(BODEX_ERR_OOM, "cudaMalloc grid");
+    }
+    e = cudaMemcpyAsync(o->grid, d->values, cnt * sizeof(float), cudaMemcpyHostToDevice, as_stream(stream));
+    if (e != cudaSuccess) {
+      cudaFree(o->grid);
+      delete o;
+      return cuda_fail(e, "cudaMemcpyAsync grid");
+    }
+    o->dev.grid = o->grid;
+  } else {
+    delete o;
+    return fail(BODEX_ERR_INVALID, "object kind must be 0 (sphere) or 1 (grid)");
+  }
+  *out = o;
+  return BODEX_OK;
+}
+
+int bodex_object_destroy(bodex_object_t o) {
+  if (!o) return BODEX_OK;
+  if (o->grid) cudaFree(o->grid);
+  delete o;
+  return BODEX_OK;
+}
+
+int bodex_object_gravity_centre(bodex_object_t o, float out[3]) {
+  if (!o || !out) return fail(BODEX_ERR_INVALID, "null argument");
+  out[0] = o->dev.gcx;
+  out[1] = o->dev.gcy;
+  out[2] = o->dev.gcz;
+  return BODEX_OK;
+}
+
+int bodex_fk_contacts(bodex_hand_t h, bodex_object_t o, const float* x, int B, float* c_w, float* p, float* n,
+                      float* phi, float* G, int32_t* cell, int32_t* status, void* stream) {
+  if (!h || !o || (!x && B > 0) || B < 0) return fail(BODEX_ERR_INVALID, "null handle/pose or B < 0");
+  cudaStream_t st = as_stream(stream);
+  switch (h->host.m) {
+    case 3: return run_fk<3>(h, o, x, B, c_w, p, n, phi, G, cell, status, st);
+    case 4: return run_fk<4>(h, o, x, B, c_w, p, n, phi, G, cell, status, st);
+    case 5: return run_fk<5>(h, o, x, B, c_w, p, n, phi, G, cell, status, st);
+  }
+  return fail(BODEX_ERR_INVALID, "unsupported m");
+}
+
+int bodex_qp_solve_batch(const float* G, int B, int m, const float* T, int s, const bodex_qp_params* params,
+                         float* y, float* z, float* lam, float* Q, int32_t* iters, int32_t* status, float* res,
+                         void* stream) {
+  if (B < 0 || s < 1 || s > SMAX) return fail(BODEX_ERR_INVALID, "B < 0 or s outside 1..16");
+  if (B > 0 && (!G || !T || !y || !z || !lam || !Q)) return fail(BODEX_ERR_INVALID, "null array");
+  if (int r = check_qp_params(params, m)) return r;
+  if (params->strict && !status) return fail(BODEX_ERR_INVALID, "strict mode needs a status array");
+  const AdmmCfg cfg = admm_cfg(*params);
+  cudaStream_t st = as_stream(stream);
+  int r;
+  switch (m) {
+    case 3: r = run_qp<3>(G, B, T, s, cfg, params->warm, y, z, lam, Q, iters, status, res, st); break;
+    case 4: r = run_qp<4>(G, B, T, s, cfg, params->warm, y, z, lam, Q, iters, status, res, st); break;
+    case 5: r = run_qp<5>(G, B, T, s, cfg, params->warm, y, z, lam, Q, iters, status, res, st); break;
+    default: return fail(BODEX_ERR_INVALID, "m must be 3, 4 or 5");
+  }
+  if (r || !params->strict || B == 0) return r;
+  std::vector<int32_t> hs((size_t)B * s);
+  BODEX_CUDA(cudaMemcpyAsync(hs.data(), status, hs.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  BODEX_CUDA(cudaStreamSynchronize(st));
+  for (int32_t v : hs)
+    if (v & BODEX_ST_NOT_CONVERGED) return fail(BODEX_ERR_NOT_CONVERGED, "a QP missed eps_abs");
+  return BODEX_OK;
+}
+
+int bodex_state_create(bodex_hand_t h, int B, int s, bodex_state_t* out) {
+  if (!h || !out || B < 0 || s < 1 || s > SMAX) return fail(BODEX_ERR_INVALID, "bad state arguments");
+  *out = nullptr;
+  bodex_state_s* S = new bodex_state_s();
+  S->B = B;
+  S->s = s;
+  S->m = h->host.m;
+  S->D = h->host.D;
+  const size_t nx = (size_t)B * S->D, ny = (size_t)B * s * 3 * S->m, nw = (size_t)B * s * (9 * S->m + 1);
+  float** bufs[5] = {&S->x, &S->am, &S->av, &S->qy, &S->qw};
+  const size_t cnt[5] = {nx, nx, nx, ny, nw};
+  for (int k = 0; k < 5; ++k) {
+    if (cnt[k] == 0) continue;
+    if (cudaMalloc(bufs[k], cnt[k] * sizeof(float)) != cudaSuccess) {
+      for (int j = 0; j < k; ++j) cudaFree(*bufs[j]);
+      delete S;
+      return fail(BODEX_ERR_OOM, "cudaMalloc state");
+    }
+    cudaMemset(*bufs[k], 0, cnt[k] * sizeof(float));
+  }
+  *out = S;
+  return BODEX_OK;
+}
+
+int bodex_state_destroy(bodex_state_t S) {
+  if (!S) return BODEX_OK;
+  cudaFree(S->x);
+  cudaFree(S->am);
+  cudaFree(S->av);
+  cudaFree(S->qy);
+  cudaFree(S->qw);
+  delete S;
+  return BODEX_OK;
+}
+
+int bodex_state_set_pose(bodex_state_t S, const float* x, void* stream) {
+  if (!S || (!x && S->B > 0)) return fail(BODEX_ERR_INVALID, "null argument");
+  if (S->B == 0) return BODEX_OK;
+  cudaStream_t st = as_stream(stream);
+  const size_t nx = (size_t)S->B * S->D;
+  BODEX_CUDA(cudaMemcpyAsync(S->x, x, nx * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  BODEX_CUDA(cudaMemsetAsync(S->am, 0, nx * sizeof(float), st));
+  BODEX_CUDA(cudaMemsetAsync(S->av, 0, nx * sizeof(float), st));
+  BODEX_CUDA(cudaMemsetAsync(S->qy, 0, (size_t)S->B * S->s * 3 * S->m * sizeof(float), st));
+  BODEX_CUDA(cudaMemsetAsync(S->qw, 0, (size_t)S->B * S->s * (9 * S->m + 1) * sizeof(float), st));
+  S->t = 0;
+  return BODEX_OK;
+}
+
+int bodex_state_get_pose(bodex_state_t S, float* x, void* stream) {
+  if (!S || (!x && S->B > 0)) return fail(BODEX_ERR_INVALID, "null argument");
+  if (S->B == 0) return BODEX_OK;
+  BODEX_CUDA(cudaMemcpyAsync(x, S->x, (size_t)S->B * S->D * sizeof(float), cudaMemcpyDeviceToDevice,
+                             as_stream(stream)));
+  return BODEX_OK;
+}
+
+int bodex_state_get_adam(bodex_state_t S, float* m, float* v, int* step, void* stream) {
+  if (!S) return fail(BODEX_ERR_INVALID, "null state");
+  const size_t nx = (size_t)S->B * S->D * sizeof(float);
+  if (m && nx) BODEX_CUDA(cudaMemcpyAsync(m, S->am, nx, cudaMemcpyDeviceToDevice, as_stream(stream)));
+  if (v && nx) BODEX_CUDA(cudaMemcpyAsync(v, S->av, nx, cudaMemcpyDeviceToDevice, as_stream(stream)));
+  if (step) *step = S->t;
+  return BODEX_OK;
+}
+
+static int fill_args(FusedArgs& A, bodex_hand_t h, bodex_object_t o, const float* T, int s, int B,
+                     const bodex_step_params* p) {
+  if (!h || !o || !p || !T || s < 1 || s > SMAX || B < 0) return fail(BODEX_ERR_INVALID, "bad arguments");
+  if (int r = check_qp_params(&p->qp, h->host.m)) return r;
+  std::memset(&A, 0, sizeof(A));
+  A.hand = h->dev;
+  A.obj = o->dev;
+  A.T = T;
+  A.S = s;
+  A.B = B;
+  A.cfg = admm_cfg(p->qp);
+  A.w_q = p->energy.w_q;
+  A.w_d = p->energy.w_d;
+  A.delta = p->energy.delta;
+  A.lr_t = p->lr_t;
+  A.lr_r = p->lr_r;
+  A.b1 = p->b1;
+  A.b2 = p->b2;
+  A.adam_eps = p->adam_eps;
+  return BODEX_OK;
+}
+
+int bodex_energy_grad(bodex_hand_t h, bodex_object_t o, const float* x, int B, const float* T, int s,
+                      const bodex_step_params* params, bodex_state_t warm, float* E, float* dEdx, float* Q,
+                      float* y, int32_t* status, void* stream) {
+  FusedArgs A;
+  if (int r = fill_args(A, h, o, T, s, B, params)) return r;
+  if (B > 0 && (!x || !E)) return fail(BODEX_ERR_INVALID, "null x or E");
+  if (warm && (warm->B != B || warm->s != s || warm->m != h->host.m))
+    return fail(BODEX_ERR_INVALID, "warm state shape mismatch");
+  A.n_steps = 1;
+  A.x_in = x;
+  A.qy = warm ? warm->qy : nullptr;
+  A.qw = warm ? warm->qw : nullptr;
+  A.E = E;
+  A.dEdx = dEdx;
+  A.Qout = Q;
+  A.yout = y;
+  A.status = status;
+  return dispatch_fused(h->host.m, MODE_EVAL, A, as_stream(stream));
+}
+
+int bodex_step(bodex_hand_t h, bodex_object_t o, bodex_state_t S, const float* T, int s, int n_steps,
+               const bodex_step_params* params, float* E_last, int32_t* status, void* stream) {
+  if (!S) return fail(BODEX_ERR_INVALID, "null state");
+  FusedArgs A;
+  if (int r = fill_args(A, h, o, T, s, S->B, params)) return r;
+  if (S->s != s || S->m != h->host.m) return fail(BODEX_ERR_INVALID, "state shape mismatch");
+  if (n_steps < 0) return fail(BODEX_ERR_INVALID, "n_steps < 0");
+  if (n_steps == 0) return BODEX_OK;
+  A.n_steps = n_steps;
+  A.t0 = S->t;
+  A.x_state = S->x;
+  A.am = S->am;
+  A.av = S->av;
+  A.qy = S->qy;
+  A.qw = S->qw;
+  A.E = E_last;
+  A.status = status;
+  const int r = dispatch_fused(h->host.m, MODE_STEP, A, as_stream(stream));
+  if (r == BODEX_OK) S->t += n_steps;
+  return r;
+}
+
+}  // extern "C"

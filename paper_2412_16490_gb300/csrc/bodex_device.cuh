@@ -1,0 +1,702 @@
+// Device-side building blocks of the BODex coarse-stage hot path (sm_103a).
+//
+// Everything here is float32 CUDA-core arithmetic.  The lower-level QPs are
+// tiny dense problems with a different matrix per grasp, so the path is not a
+// shared dense contraction and does not use the tensor cores; the per-grasp
+// data (G, K^-1) lives in shared memory and the per-QP ADMM iterate in
+// registers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bodex.h"
+
+namespace bodex {
+
+constexpr int MAXJ = BODEX_MAX_JOINTS;
+constexpr int MAXM = BODEX_MAX_CONTACTS;
+constexpr int MAXCHAIN = BODEX_MAX_CHAIN;
+constexpr int MAXD = 6 + MAXJ;
+constexpr int SMAX = 16;  // wrenches per grasp
+
+// cos / sin of pi/8: the facet normals of the 8-edge pyramid sit at
+// phi_k = (2k+1) pi/8 in the contact's (d, e) plane.
+constexpr float C8 = 0.92387953251128674f;
+constexpr float S8 = 0.38268343236508978f;
+
+// ------------------------------------------------------------------ handles
+struct HandDev {
+  int n, m, D, S;
+  float alpha;
+  int parent[MAXJ];
+  float offset[MAXJ][12];
+  float axis[MAXJ][3];
+  float qmin[MAXD], qmax[MAXD];
+  int clink[MAXM];
+  float clocal[MAXM][3];
+  int chain_len[MAXM];
+  int chain[MAXM][MAXCHAIN];  // joints from the root to contact i's link
+  int8_t jpos[MAXM][MAXJ];    // position of joint j in contact i's chain, or -1
+};
+
+struct ObjDev {
+  int kind;  // 0 sphere, 1 grid
+  float cx, cy, cz, r;
+  int N;
+  float h, inv_h;
+  float ox, oy, oz;
+  const float* grid;
+  float gcx, gcy, gcz;  // gravity centre
+};
+
+struct AdmmCfg {
+  float mu_c8;  // mu cos(pi/8)
+  float beta, gamma, rho, sigma, alpha, eps, eps_reg;
+  int iters, check;
+};
+
+__host__ __device__ inline AdmmCfg admm_cfg(const bodex_qp_params& p) {
+  AdmmCfg c;
+  c.mu_c8 = p.mu * C8;
+  c.beta = p.beta;
+  c.gamma = p.gamma;
+  c.rho = p.rho;
+  c.sigma = p.sigma;
+  c.alpha = p.alpha;
+  c.eps = p.eps_abs;
+  c.eps_reg = p.eps_reg;
+  c.iters = p.max_iter;
+  c.check = p.check_every > 0 ? p.check_every : 10;
+  return c;
+}
+
+// ------------------------------------------------------------------ rigid transforms
+struct Tf {
+  float R[9];
+  float t[3];
+};
+
+__device__ __forceinline__ void tf_mul(const Tf& A, const Tf& B, Tf& C) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+      C.R[3 * r + c] = fmaf(A.R[3 * r], B.R[c], fmaf(A.R[3 * r + 1], B.R[3 + c], A.R[3 * r + 2] * B.R[6 + c]));
+    C.t[r] = fmaf(A.R[3 * r], B.t[0], fmaf(A.R[3 * r + 1], B.t[1], fmaf(A.R[3 * r + 2], B.t[2], A.t[r])));
+  }
+}
+
+__device__ __forceinline__ void rot_vec(const float* R, const float* v, float* o) {
+  o[0] = fmaf(R[0], v[0], fmaf(R[1], v[1], R[2] * v[2]));
+  o[1] = fmaf(R[3], v[0], fmaf(R[4], v[1], R[5] * v[2]));
+  o[2] = fmaf(R[6], v[0], fmaf(R[7], v[1], R[8] * v[2]));
+}
+
+// Rotation by q about the unit axis a (Rodrigues).
+__device__ __forceinline__ void rodrigues(const float* a, float q, float* R) {
+  float s, c;
+  sincosf(q, &s, &c);
+  const float C = 1.0f - c;
+  R[0] = c + a[0] * a[0] * C;
+  R[1] = a[0] * a[1] * C - a[2] * s;
+  R[2] = a[0] * a[2] * C + a[1] * s;
+  R[3] = a[1] * a[0] * C + a[2] * s;
+  R[4] = c + a[1] * a[1] * C;
+  R[5] = a[1] * a[2] * C - a[0] * s;
+  R[6] = a[2] * a[0] * C - a[1] * s;
+  R[7] = a[2] * a[1] * C + a[0] * s;
+  R[8] = c + a[2] * a[2] * C;
+}
+
+// Root frame Trans(t) Rx(rx) Ry(ry) Rz(rz) and the world axes of the three
+// virtual revolute joints (rx about world X, ry about Rx Y, rz about Rx Ry Z).
+__device__ __forceinline__ void root_frame(const float* x, Tf& T, float om[3][3]) {
+  float s1, c1, s2, c2, s3, c3;
+  sincosf(x[3], &s1, &c1);
+  sincosf(x[4], &s2, &c2);
+  sincosf(x[5], &s3, &c3);
+  T.R[0] = c2 * c3;
+  T.R[1] = -c2 * s3;
+  T.R[2] = s2;
+  T.R[3] = s1 * s2 * c3 + c1 * s3;
+  T.R[4] = -s1 * s2 * s3 + c1 * c3;
+  T.R[5] = -s1 * c2;
+  T.R[6] = -c1 * s2 * c3 + s1 * s3;
+  T.R[7] = c1 * s2 * s3 + s1 * c3;
+  T.R[8] = c1 * c2;
+  T.t[0] = x[0];
+  T.t[1] = x[1];
+  T.t[2] = x[2];
+  om[0][0] = 1.f; om[0][1] = 0.f; om[0][2] = 0.f;
+  om[1][0] = 0.f; om[1][1] = c1;  om[1][2] = s1;
+  om[2][0] = s2;  om[2][1] = -s1 * c2; om[2][2] = c1 * c2;
+}
+
+// Forward kinematics for contact i (Sec. IV-B): walks the chain from the
+// root to the contact link.  Returns c_{i,w}; if `jw` is given, stores the
+// world axis and a point on the axis of every chain joint (6 floats each,
+// in chain order) for the adjoint.
+__device__ inline void fk_contact(const HandDev& H, int i, const float* x, float* c, float* jw) {
+  Tf T;
+  float om[3][3];
+  root_frame(x, T, om);
+  const int L = H.chain_len[i];
+  for (int k = 0; k < L; ++k) {
+    const int j = H.chain[i][k];
+    Tf off;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+      for (int cc = 0; cc < 3; ++cc) off.R[3 * r + cc] = H.offset[j][4 * r + cc];
+      off.t[r] = H.offset[j][4 * r + 3];
+    }
+    Tf base;
+    tf_mul(T, off, base);
+    const float a[3] = {H.axis[j][0], H.axis[j][1], H.axis[j][2]};
+    if (jw) {
+      rot_vec(base.R, a, jw + 6 * k);
+      jw[6 * k + 3] = base.t[0];
+      jw[6 * k + 4] = base.t[1];
+      jw[6 * k + 5] = base.t[2];
+    }
+    Tf rq;
+    rodrigues(a, x[6 + j], rq.R);
+    rq.t[0] = rq.t[1] = rq.t[2] = 0.f;
+    tf_mul(base, rq, T);
+  }
+  const float* cl = H.clocal[i];
+  c[0] = fmaf(T.R[0], cl[0], fmaf(T.R[1], cl[1], fmaf(T.R[2], cl[2], T.t[0])));
+  c[1] = fmaf(T.R[3], cl[0], fmaf(T.R[4], cl[1], fmaf(T.R[5], cl[2], T.t[1])));
+  c[2] = fmaf(T.R[6], cl[0], fmaf(T.R[7], cl[1], fmaf(T.R[8], cl[2], T.t[2])));
+}
+
+// ------------------------------------------------------------------ SDF query
+// phi, gradient g, Hessian h (xx, xy, xz, yy, yz, zz) and voxel cell at c.
+// Grid: node-sampled trilinear interpolant; outside the node box
+// phi(c) = phi(clamp(c)) + |c - clamp(c)| with the exact derivatives of that
+// expression.
+struct SdfQ {
+  float phi;
+  float g[3];
+  float h[6];
+  int cell[3];
+};
+
+__device__ inline SdfQ sdf_query(const ObjDev& O, const float* c) {
+  SdfQ q;
+  if (O.kind == 0) {
+    const float v0 = c[0] - O.cx, v1 = c[1] - O.cy, v2 = c[2] - O.cz;
+    const float L = sqrtf(v0 * v0 + v1 * v1 + v2 * v2);
+    const float iL = 1.0f / L;
+    const float u0 = v0 * iL, u1 = v1 * iL, u2 = v2 * iL;
+    q.phi = L - O.r;
+    q.g[0] = u0; q.g[1] = u1; q.g[2] = u2;
+    q.h[0] = (1.f - u0 * u0) * iL;
+    q.h[1] = -u0 * u1 * iL;
+    q.h[2] = -u0 * u2 * iL;
+    q.h[3] = (1.f - u1 * u1) * iL;
+    q.h[4] = -u1 * u2 * iL;
+    q.h[5] = (1.f - u2 * u2) * iL;
+    q.cell[0] = q.cell[1] = q.cell[2] = 0;
+    return q;
+  }
+  const int N = O.N;
+  const float org[3] = {O.ox, O.oy, O.oz};
+  const float hi_off = O.h * (float)(N - 1);
+  float cl[3], t[3], dv[3];
+  bool cla[3];
+  int cell[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float lo = org[a], hi = org[a] + hi_off;
+    cla[a] = (c[a] < lo) || (c[a] > hi);
+    cl[a] = fminf(fmaxf(c[a], lo), hi);
+    const float u = (cl[a] - org[a]) / O.h;
+    int k = (int)floorf(u);
+    k = min(max(k, 0), N - 2);
+    cell[a] = k;
+    t[a] = u - (float)k;
+    dv[a] = c[a] - cl[a];
+  }
+  const float* G0 = O.grid + ((size_t)cell[2] * N + cell[1]) * N + cell[0];
+  const size_t sy = N, sz = (size_t)N * N;
+  const float v000 = __ldg(G0), v100 = __ldg(G0 + 1);
+  const float v010 = __ldg(G0 + sy), v110 = __ldg(G0 + sy + 1);
+  const float v001 = __ldg(G0 + sz), v101 = __ldg(G0 + sz + 1);
+  const float v011 = __ldg(G0 + sz + sy), v111 = __ldg(G0 + sz + sy + 1);
+  const float tx = t[0], ty = t[1], tz = t[2];
+  // interpolate along x, then y, then z
+  const float a00 = fmaf(tx, v100 - v000, v000), a10 = fmaf(tx, v110 - v010, v010);
+  const float a01 = fmaf(tx, v101 - v001, v001), a11 = fmaf(tx, v111 - v011, v011);
+  const float b0 = fmaf(ty, a10 - a00, a00), b1 = fmaf(ty, a11 - a01, a01);
+  const float phi_cl = fmaf(tz, b1 - b0, b0);
+  // d/dx: differences along x, interpolated in y, z
+  const float dx00 = v100 - v000, dx10 = v110 - v010, dx01 = v101 - v001, dx11 = v111 - v011;
+  const float dxb0 = fmaf(ty, dx10 - dx00, dx00), dxb1 = fmaf(ty, dx11 - dx01, dx01);
+  const float gx = fmaf(tz, dxb1 - dxb0, dxb0) * O.inv_h;
+  const float gy = fmaf(tz, a11 - a01 - (a10 - a00), a10 - a00) * O.inv_h;
+  const float gz = (b1 - b0) * O.inv_h;
+  // mixed second derivatives (the pure ones vanish for a trilinear cell)
+  const float hxy = fmaf(tz, (dx11 - dx01) - (dx10 - dx00), dx10 - dx00) * O.inv_h * O.inv_h;
+  const float hxz = (dxb1 - dxb0) * O.inv_h * O.inv_h;
+  const float hyz = ((a11 - a01) - (a10 - a00)) * O.inv_h * O.inv_h;
+  const float gcl[3] = {gx, gy, gz};
+  const float hcl[6] = {0.f, hxy, hxz, 0.f, hyz, 0.f};
+  const float dl2 = dv[0] * dv[0] + dv[1] * dv[1] + dv[2] * dv[2];
+  const bool any = cla[0] || cla[1] || cla[2];
+  const float dl = any ? sqrtf(dl2) : 0.f;
+  const float idl = any ? 1.0f / dl : 0.f;
+  q.phi = phi_cl + dl;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    q.g[a] = cla[a] ? dv[a] * idl : gcl[a];
+    q.cell[a] = cell[a];
+  }
+  // Hessian entries (a, b) in order xx, xy, xz, yy, yz, zz
+  const int ia[6] = {0, 0, 0, 1, 1, 2}, ib[6] = {0, 1, 2, 1, 2, 2};
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const int a = ia[e], b = ib[e];
+    float v = 0.f;
+    if (!cla[a] && !cla[b]) v = hcl[e];
+    else if (cla[a] && cla[b]) v = ((a == b ? 1.f : 0.f) - dv[a] * dv[b] * idl * idl) * idl;
+    q.h[e] = v;
+  }
+  return q;
+}
+
+// Tangent basis (d, e) of a unit normal n with n = d x e: the branch-free
+// construction of Duff et al., "Building an Orthonormal Basis, Revisited"
+// (JCGT 2017), sign taken from n_z.
+__device__ __forceinline__ void tangent_basis(const float* n, float* d, float* e) {
+  const float sg = copysignf(1.0f, n[2]);
+  const float a = -1.0f / (sg + n[2]);
+  const float b = n[0] * n[1] * a;
+  d[0] = 1.0f + sg * n[0] * n[0] * a;
+  d[1] = sg * b;
+  d[2] = -sg * n[0];
+  e[0] = b;
+  e[1] = sg + n[1] * n[1] * a;
+  e[2] = -n[1];
+}
+
+__device__ __forceinline__ void cross3(const float* a, const float* b, float* o) {
+  o[0] = a[1] * b[2] - a[2] * b[1];
+  o[1] = a[2] * b[0] - a[0] * b[2];
+  o[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+// Per-contact geometry kept between the forward pass and the adjoint.
+struct ContactGeo {
+  float c[3], p[3], n[3];  // p relative to the gravity centre
+  float phi, g[3], h[6];
+  int cell[3];
+  int degenerate;
+};
+
+// Nearest-point query (Sec. IV-B): p = c - phi g/|g|, inward n = -g/|g|.
+__device__ inline ContactGeo contact_geometry(const ObjDev& O, const float* c) {
+  ContactGeo k;
+  const SdfQ q = sdf_query(O, c);
+  const float L = sqrtf(q.g[0] * q.g[0] + q.g[1] * q.g[1] + q.g[2] * q.g[2]);
+  k.degenerate = !(L >= 1e-12f);
+  const float iL = 1.0f / L;
+  const float gc[3] = {O.gcx, O.gcy, O.gcz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float no = q.g[a] * iL;
+    k.c[a] = c[a];
+    k.n[a] = -no;
+    k.p[a] = (c[a] - q.phi * no) - gc[a];
+    k.g[a] = q.g[a];
+    k.cell[a] = q.cell[a];
+  }
+  k.phi = q.phi;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) k.h[e] = q.h[e];
+  return k;
+}
+
+// Columns 3i..3i+2 of the grasp matrix (Sec. III, Eq. (2)):
+// [n d e ; p x n, p x d, p x e], written to G (6 x nv, row-major).
+__device__ __forceinline__ void write_G_block(const ContactGeo& k, int i, int nv, float* G) {
+  float d[3], e[3];
+  tangent_basis(k.n, d, e);
+  const float* cols[3] = {k.n, d, e};
+#pragma unroll
+  for (int cidx = 0; cidx < 3; ++cidx) {
+    float tq[3];
+    cross3(k.p, cols[cidx], tq);
+    const int col = 3 * i + cidx;
+    G[0 * nv + col] = cols[cidx][0];
+    G[1 * nv + col] = cols[cidx][1];
+    G[2 * nv + col] = cols[cidx][2];
+    G[3 * nv + col] = tq[0];
+    G[4 * nv + col] = tq[1];
+    G[5 * nv + col] = tq[2];
+  }
+}
+
+// ------------------------------------------------------------------ QP setup
+// K = P + sigma I + rho A^T A with P = 2 G^T G (+ 2 eps_reg I).  For the
+// pyramid rows A^T A is the constant
+//   diag per contact (1 + 8 mu^2 cos^2(pi/8), 4, 4)  (f_n row + 8 facets)
+//   + 1 on every (f_{i,n}, f_{k,n}) pair              (the sum row),
+// because the facet normals sum to zero and their squares to 4 per axis.
+// One lane factors K (Cholesky) into Lf; the lanes of the grasp then solve
+// for the columns of K^-1 (stored in rows of stride ld).
+template <int M>
+__device__ inline void build_K(const float* G, const AdmmCfg& c, float* K) {
+  constexpr int NV = 3 * M;
+  const float dn = 1.0f + 8.0f * c.mu_c8 * c.mu_c8 + 1.0f;  // f_n row, facets, sum row
+  for (int a = 0; a < NV; ++a)
+    for (int b = a; b < NV; ++b) {
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < 6; ++r) s = fmaf(G[r * NV + a], G[r * NV + b], s);
+      float v = 2.0f * s;
+      if (a == b) {
+        v += c.sigma + 2.0f * c.eps_reg;
+        v += c.rho * ((a % 3 == 0) ? dn : 4.0f);
+      } else if ((a % 3 == 0) && (b % 3 == 0)) {
+        v += c.rho;  // sum row couples the normal components
+      }
+      K[a * NV + b] = v;
+      K[b * NV + a] = v;
+    }
+}
+
+// In-place Cholesky K = L L^T (lower triangle of K receives L).  Returns
+// false on a non-positive pivot.
+template <int NV>
+__device__ inline bool cholesky(float* K) {
+  bool ok = true;
+  for (int j = 0; j < NV; ++j) {
+    float s = K[j * NV + j];
+    for (int k = 0; k < j; ++k) s = fmaf(-K[j * NV + k], K[j * NV + k], s);
+    if (!(s > 0.f)) {
+      ok = false;
+      s = 1e-30f;
+    }
+    const float ljj = sqrtf(s);
+    K[j * NV + j] = ljj;
+    const float il = 1.0f / ljj;
+    for (int i = j + 1; i < NV; ++i) {
+      float t = K[i * NV + j];
+      for (int k = 0; k < j; ++k) t = fmaf(-K[i * NV + k], K[j * NV + k], t);
+      K[i * NV + j] = t * il;
+    }
+  }
+  return ok;
+}
+
+// Column `col` of K^-1 from the Cholesky factor: solve L L^T v = e_col and
+// store v as column col of Kinv (row stride ld).  K^-1 is symmetric, so the
+// column is also row col.
+template <int NV>
+__device__ inline void chol_inverse_column(const float* L, int col, float* Kinv, int ld) {
+  float v[NV];
+#pragma unroll
+  for (int i = 0; i < NV; ++i) {
+    float s = (i == col) ? 1.0f : 0.0f;
+#pragma unroll
+    for (int k = 0; k < i; ++k) s = fmaf(-L[i * NV + k], v[k], s);
+    v[i] = s / L[i * NV + i];
+  }
+#pragma unroll
+  for (int i = NV - 1; i >= 0; --i) {
+    float s = v[i];
+#pragma unroll
+    for (int k = i + 1; k < NV; ++k) s = fmaf(-L[k * NV + i], v[k], s);
+    v[i] = s / L[i * NV + i];
+  }
+#pragma unroll
+  for (int i = 0; i < NV; ++i) Kinv[i * ld + col] = v[i];
+}
+
+// ------------------------------------------------------------------ ADMM
+// One QP per thread.  State: y (nv) and w (nc) with z = Pi(w),
+// lam = rho (w - Pi(w)) (Pi: projection onto [l, u]).  With that state the
+// OSQP iteration (Stellato et al. 2020, Alg. 1) reads
+//   rhs = sigma y - q + rho A^T (2 Pi(w) - w)
+//   yt  = K^-1 rhs,   zt = A yt
+//   y  <- alpha yt + (1 - alpha) y
+//   w  <- w + alpha (zt - Pi(w)).
+// Row order of A: per contact [f_n, facet 0..7], then the sum row.
+// 16-byte shared-memory load kept inside the loop that issues it.  K^-1 is
+// loop-invariant across ADMM iterations; left to itself the compiler hoists
+// all of it into registers, which does not fit next to the iterate.
+__device__ __forceinline__ float4 lds128(const float* p) {
+  float4 v;
+  const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+               : "r"(addr));
+  return v;
+}
+
+__device__ __forceinline__ float lds32(const float* p) {
+  float v;
+  const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
+  return v;
+}
+
+template <int M>
+struct Admm {
+  static constexpr int NV = 3 * M;
+  static constexpr int NC = 9 * M + 1;
+  static constexpr int NVP = (NV + 3) & ~3;
+};
+
+__device__ constexpr float kFC[8] = {C8, S8, -S8, -C8, -C8, -S8, S8, C8};
+__device__ constexpr float kFS[8] = {S8, C8, C8, S8, -S8, -C8, -C8, -S8};
+
+template <int M>
+__device__ __forceinline__ float proj_row(float w, int row, float gamma) {
+  // [l, u] per row: f_n in [0, 1], facets in (-inf, 0], sum row in [gamma, inf)
+  if (row == 9 * M) return fmaxf(w, gamma);
+  if (row % 9 == 0) return fminf(fmaxf(w, 0.f), 1.f);
+  return fminf(w, 0.f);
+}
+
+// Contribution of one contact's nine rows (v0: the f_n row, vk: the facets)
+// to A^T v.  The sum row's entry is added to the normal component by the caller.
+__device__ __forceinline__ void At_contact(float v0, const float (&vk)[8], float mu_c8, float& gn, float& gd,
+                                           float& ge) {
+  const float sum = ((vk[0] + vk[1]) + (vk[2] + vk[3])) + ((vk[4] + vk[5]) + (vk[6] + vk[7]));
+  gn = fmaf(-mu_c8, sum, v0);
+  gd = C8 * ((vk[0] + vk[7]) - (vk[3] + vk[4])) + S8 * ((vk[1] + vk[6]) - (vk[2] + vk[5]));
+  ge = S8 * ((vk[0] + vk[3]) - (vk[4] + vk[7])) + C8 * ((vk[1] + vk[2]) - (vk[5] + vk[6]));
+}
+
+template <int M>
+__device__ __forceinline__ void admm_iteration(float* y, float* w, const float* mq, const float* Kinv,
+                                               const AdmmCfg& c) {
+  constexpr int NV = Admm<M>::NV, NVP = Admm<M>::NVP;
+  // rhs = sigma y - q + rho A^T (2 Pi(w) - w), one contact at a time
+  float rhs[NV];
+  const float vsum = 2.f * fmaxf(w[9 * M], c.gamma) - w[9 * M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const float v0 = 2.f * fminf(fmaxf(w[9 * i], 0.f), 1.f) - w[9 * i] + vsum;
+    float vk[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) vk[k] = 2.f * fminf(w[9 * i + 1 + k], 0.f) - w[9 * i + 1 + k];
+    float gn, gd, ge;
+    At_contact(v0, vk, c.mu_c8, gn, gd, ge);
+    rhs[3 * i] = fmaf(c.sigma, y[3 * i], fmaf(c.rho, gn, mq[3 * i]));
+    rhs[3 * i + 1] = fmaf(c.sigma, y[3 * i + 1], fmaf(c.rho, gd, mq[3 * i + 1]));
+    rhs[3 * i + 2] = fmaf(c.sigma, y[3 * i + 2], fmaf(c.rho, ge, mq[3 * i + 2]));
+  }
+  // yt = K^-1 rhs (rows of K^-1 from shared memory, 16-byte loads)
+  float yt[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+    for (int q = 0; q < NVP / 4; ++q) {
+      const float4 k4 = lds128(Kinv + a * NVP + 4 * q);
+      const int b = 4 * q;
+      if (b + 0 < NV) s0 = fmaf(k4.x, rhs[b + 0], s0);
+      if (b + 1 < NV) s1 = fmaf(k4.y, rhs[b + 1], s1);
+      if (b + 2 < NV) s0 = fmaf(k4.z, rhs[b + 2], s0);
+      if (b + 3 < NV) s1 = fmaf(k4.w, rhs[b + 3], s1);
+    }
+    yt[a] = s0 + s1;
+  }
+  // w <- w + alpha (A yt - Pi(w)),  y <- alpha yt + (1 - alpha) y
+  const float al = c.alpha, bl = 1.0f - c.alpha;
+  float sumn = 0.f;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const float tn = yt[3 * i], td = yt[3 * i + 1], te = yt[3 * i + 2];
+    sumn += tn;
+    {
+      const float p = fminf(fmaxf(w[9 * i], 0.f), 1.f);
+      w[9 * i] = fmaf(al, tn - p, w[9 * i]);
+    }
+    const float base = -c.mu_c8 * tn;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float zt = fmaf(kFC[k], td, fmaf(kFS[k], te, base));
+      const float p = fminf(w[9 * i + 1 + k], 0.f);
+      w[9 * i + 1 + k] = fmaf(al, zt - p, w[9 * i + 1 + k]);
+    }
+  }
+  {
+    const float p = fmaxf(w[9 * M], c.gamma);
+    w[9 * M] = fmaf(al, sumn - p, w[9 * M]);
+  }
+#pragma unroll
+  for (int a = 0; a < NV; ++a) y[a] = fmaf(al, yt[a], bl * y[a]);
+}
+
+// Infinity-norm residuals at (y, w): primal |A y - z|, dual |P y + q + A^T lam|,
+// z = Pi(w), lam = rho (w - Pi(w)).
+template <int M>
+__device__ inline void admm_residuals(const float* y, const float* w, const float* mq, const float* G,
+                                      const AdmmCfg& c, float& rp, float& rd) {
+  constexpr int NV = Admm<M>::NV;
+  rp = 0.f;
+  float sumn = 0.f;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const float yn = y[3 * i], yd = y[3 * i + 1], ye = y[3 * i + 2];
+    sumn += yn;
+    rp = fmaxf(rp, fabsf(yn - fminf(fmaxf(w[9 * i], 0.f), 1.f)));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float ay = fmaf(kFC[k], yd, fmaf(kFS[k], ye, -c.mu_c8 * yn));
+      rp = fmaxf(rp, fabsf(ay - fminf(w[9 * i + 1 + k], 0.f)));
+    }
+  }
+  rp = fmaxf(rp, fabsf(sumn - fmaxf(w[9 * M], c.gamma)));
+  float gy[6];
+#pragma unroll
+  for (int r = 0; r < 6; ++r) {
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) s = fmaf(lds32(G + r * NV + a), y[a], s);
+    gy[r] = s;
+  }
+  const float lsum = c.rho * (w[9 * M] - fmaxf(w[9 * M], c.gamma));
+  rd = 0.f;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const float l0 = c.rho * (w[9 * i] - fminf(fmaxf(w[9 * i], 0.f), 1.f)) + lsum;
+    float lk[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) lk[k] = c.rho * (w[9 * i + 1 + k] - fminf(w[9 * i + 1 + k], 0.f));
+    float at[3];
+    At_contact(l0, lk, c.mu_c8, at[0], at[1], at[2]);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int a = 3 * i + q;
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < 6; ++r) s = fmaf(lds32(G + r * NV + a), gy[r], s);
+      const float py = 2.f * s + 2.f * c.eps_reg * y[a];
+      rd = fmaxf(rd, fabsf(py - mq[a] + at[q]));
+    }
+  }
+}
+
+// -q = 2 beta G^T t for one wrench t.
+template <int M>
+__device__ __forceinline__ void neg_q(const float* G, const float* t, float beta, float* mq) {
+  constexpr int NV = 3 * M;
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    float s = 0.f;
+#pragma unroll
+    for (int r = 0; r < 6; ++r) s = fmaf(G[r * NV + a], t[r], s);
+    mq[a] = 2.f * beta * s;
+  }
+}
+
+// Runs ADMM on one QP until both residuals are <= eps (checked every
+// `check` iterations, eps > 0) or `iters` iterations.  Returns the count
+// used; rp/rd receive the last residuals (computed once at the end when
+// eps == 0).
+template <int M>
+__device__ inline int admm_solve(float* y, float* w, const float* mq, const float* Kinv, const float* G,
+                                 const AdmmCfg& c, float& rp, float& rd, bool& conv) {
+  int it = 0;
+  conv = false;
+  rp = rd = 0.f;
+  if (c.eps > 0.f) {
+#pragma unroll 1
+    while (it < c.iters) {
+      const int chunk = min(c.check, c.iters - it);
+#pragma unroll 1
+      for (int k = 0; k < chunk; ++k) admm_iteration<M>(y, w, mq, Kinv, c);
+      it += chunk;
+      admm_residuals<M>(y, w, mq, G, c, rp, rd);
+      if (rp <= c.eps && rd <= c.eps) {
+        conv = true;
+        break;
+      }
+    }
+  } else {
+#pragma unroll 1
+    for (; it < c.iters; ++it) admm_iteration<M>(y, w, mq, Kinv, c);
+    admm_residuals<M>(y, w, mq, G, c, rp, rd);
+  }
+  return it;
+}
+
+// ------------------------------------------------------------------ adjoint
+// Envelope-theorem gradient through one contact (Secs. III, IV-A):
+// given dE/dG for the contact's three columns (a_k force half, b_k torque
+// half, v_k in {n, d, e}):
+//   dE/dp = sum_k v_k x b_k,   dE/dv_k = a_k + b_k x p,
+// then through the tangent basis d(n), e(n), the normal n = -g/|g| and the
+// point p = c - phi g/|g| (g, Hs: SDF gradient and Hessian), plus the
+// distance term 2 w_d (phi - alpha - delta) g.  Returns dE/dc.
+__device__ inline void contact_adjoint(const ContactGeo& k, const float* dEdG_cols /* [6][3] */,
+                                       float dist_coef, float* dEdc) {
+  float d[3], e[3];
+  tangent_basis(k.n, d, e);
+  const float* vk[3] = {k.n, d, e};
+  float dEdp[3] = {0.f, 0.f, 0.f};
+  float dEdv[3][3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const float a[3] = {dEdG_cols[0 * 3 + q], dEdG_cols[1 * 3 + q], dEdG_cols[2 * 3 + q]};
+    const float b[3] = {dEdG_cols[3 * 3 + q], dEdG_cols[4 * 3 + q], dEdG_cols[5 * 3 + q]};
+    float vb[3], bp[3];
+    cross3(vk[q], b, vb);
+    cross3(b, k.p, bp);
+#pragma unroll
+    for (int t = 0; t < 3; ++t) {
+      dEdp[t] += vb[t];
+      dEdv[q][t] = a[t] + bp[t];
+    }
+  }
+  // basis Jacobians (derivative of the Duff construction with the sign fixed)
+  const float nx = k.n[0], ny = k.n[1], nz = k.n[2];
+  const float sg = copysignf(1.0f, nz);
+  const float a = -1.0f / (sg + nz);
+  const float a2 = a * a;
+  const float Jd[3][3] = {{2.f * sg * nx * a, 0.f, sg * nx * nx * a2},
+                          {sg * ny * a, sg * nx * a, sg * nx * ny * a2},
+                          {-sg, 0.f, 0.f}};
+  const float Je[3][3] = {{ny * a, nx * a, nx * ny * a2}, {0.f, 2.f * ny * a, ny * ny * a2}, {0.f, -1.f, 0.f}};
+  float dEdn[3];
+#pragma unroll
+  for (int cc = 0; cc < 3; ++cc) {
+    float s = dEdv[0][cc];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) s = fmaf(Jd[r][cc], dEdv[1][r], fmaf(Je[r][cc], dEdv[2][r], s));
+    dEdn[cc] = s;
+  }
+  // through p(c), n(c)
+  const float L = sqrtf(k.g[0] * k.g[0] + k.g[1] * k.g[1] + k.g[2] * k.g[2]);
+  const float iL = 1.0f / L;
+  const float no[3] = {k.g[0] * iL, k.g[1] * iL, k.g[2] * iL};
+  const float Hs[3][3] = {{k.h[0], k.h[1], k.h[2]}, {k.h[1], k.h[3], k.h[4]}, {k.h[2], k.h[4], k.h[5]}};
+  float Dno[3][3];  // (I - no no^T) Hs / L
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc) {
+      float s = 0.f;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) s = fmaf((r == q ? 1.f : 0.f) - no[r] * no[q], Hs[q][cc], s);
+      Dno[r][cc] = s * iL;
+    }
+#pragma unroll
+  for (int cc = 0; cc < 3; ++cc) {
+    float s = 0.f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const float dp = (r == cc ? 1.f : 0.f) - no[r] * k.g[cc] - k.phi * Dno[r][cc];
+      s = fmaf(dp, dEdp[r], fmaf(-Dno[r][cc], dEdn[r], s));
+    }
+    dEdc[cc] = fmaf(dist_coef, k.g[cc], s);
+  }
+}
+
+}  // namespace bodex

@@ -202,9 +202,11 @@ def run_ours(args, rank, world, local_rank):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
+    n_up = args.upper_steps
+
     def one_run():
         st.set_pose(x_dev)
-        bx.bodex_step(H, Ob, st, T_dev, N_STEPS, sp, E_last=E_dev, status=stat_dev)
+        bx.bodex_step(H, Ob, st, T_dev, n_up, sp, E_last=E_dev, status=stat_dev)
 
     for _ in range(args.warmup):
         one_run()
@@ -221,7 +223,7 @@ def run_ours(args, rank, world, local_rank):
             a.record(stream)
             st.set_pose(x_dev)
             k0.record(stream)
-            bx.bodex_step(H, Ob, st, T_dev, N_STEPS, sp, E_last=E_dev, status=stat_dev)
+            bx.bodex_step(H, Ob, st, T_dev, n_up, sp, E_last=E_dev, status=stat_dev)
             k1.record(stream)
             b.record(stream)
         torch.cuda.synchronize()
@@ -233,10 +235,10 @@ def run_ours(args, rank, world, local_rank):
         t = torch.tensor([mean_step], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         mean_step = float(t.item())
-    value = world * B / (mean_step / 1e3)
+    value = world * B / (mean_step / 1e3) * (n_up / N_STEPS)
 
     # roofline of the fused step kernel (the only kernel of the timed step)
-    fl = flops_per_grasp_step(hand.n_contacts, hand.n_joints, S, ADMM_ITERS) * B * N_STEPS
+    fl = flops_per_grasp_step(hand.n_contacts, hand.n_joints, S, ADMM_ITERS) * B * n_up
     kern_s = float(np.mean(kern_ms)) / 1e3
     clocks = clk.summary()
     peaks = measured_peaks()
@@ -340,6 +342,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--quick", action="store_true", help="skip the QP and e2e side measurements")
+    ap.add_argument("--upper-steps", type=int, default=N_STEPS,
+                    help="upper iterations per run (200 for the bench line; fewer for profiler captures)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))

@@ -32,7 +32,7 @@ def build(force: bool = False) -> str:
     """Compile the oracle shared library (g++, -O2) if it is missing or stale."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-pthread",
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-shared", "-fPIC", "-pthread",
                                _SRC, "-o", tmp])
         os.replace(tmp, _LIB)
     return _LIB

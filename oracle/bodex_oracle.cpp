@@ -29,7 +29,7 @@
 // orientation, tangent basis, pose parametrisation, SDF conventions) are
 // stated next to the code that takes them.
 //
-// Build:  g++ -O2 -std=c++17 -shared -fPIC -pthread bodex_oracle.cpp -o libbodex_oracle.so
+// Build:  g++ -O2 -std=c++17 -ffp-contract=off -shared -fPIC -pthread bodex_oracle.cpp -o libbodex_oracle.so
 
 #include <algorithm>
 #include <cmath>
@@ -583,7 +583,10 @@ void ls_step(const QPProblem& Pb, const Vec& Z, int k, const double* y, double e
     sig[j] = std::sqrt(s2);
     smax = std::max(smax, sig[j]);
   }
-  const double tol = 1e-12 * std::max(smax, 1.0);
+  // Singular values below this are treated as zero curvature: along them
+  // the objective's slope is at most 2 tol |rhs|, and a Newton step of
+  // (u^T rhs) / sigma would be dominated by rounding.
+  const double tol = 1e-10 * std::max(smax, 1.0);
   Vec v(k, 0.0);
   for (int j = 0; j < k; ++j) {
     if (sig[j] <= tol) continue;
@@ -651,18 +654,48 @@ QPResult qp_active_set(const QPProblem& Pb) {
       g[a] = s;
     }
     working_set_factors(Pb, W, Z, k, Qf, Rf);
-    ls_step(Pb, Z, k, R.y.data(), Pb.eps, p);
-    // The subproblem minimum is reached (p = 0 up to rounding) when the step
-    // is negligible or the model decrease -(g^T p + p^T P p / 2) is at
-    // rounding level; the final KKT certificate checks the outcome.
-    double pmax = 0, gp = 0, pPp = 0;
-    for (int a = 0; a < nv; ++a) {
-      pmax = std::max(pmax, std::fabs(p[a]));
-      gp += g[a] * p[a];
-      for (int b = 0; b < nv; ++b) pPp += p[a] * Pb.P[(size_t)a * nv + b] * p[b];
+    // Stationary on the working set when the reduced gradient Z^T g vanishes
+    // (to rounding); otherwise step toward the subproblem minimiser.
+    double gmax = 0, zg = 0;
+    for (int a = 0; a < nv; ++a) gmax = std::max(gmax, std::fabs(g[a]));
+    for (int j = 0; j < k; ++j) {
+      double v = 0;
+      for (int a = 0; a < nv; ++a) v += Z[(size_t)a * k + j] * g[a];
+      zg = std::max(zg, std::fabs(v));
     }
-    const double model_dec = -(gp + 0.5 * pPp);
-    if (pmax <= 1e-12 || model_dec <= 1e-22) {
+    bool stationary = zg <= 1e-11 * std::max(1.0, gmax);
+    if (!stationary) {
+      ls_step(Pb, Z, k, R.y.data(), Pb.eps, p);
+      double pm = 0;
+      for (int a = 0; a < nv; ++a) pm = std::max(pm, std::fabs(p[a]));
+      stationary = pm <= 1e-14;  // at the rounding floor: no step left to take
+    }
+    double pmax = 0, gp = 0, pPp = 0;
+    if (!stationary)
+      for (int a = 0; a < nv; ++a) {
+        pmax = std::max(pmax, std::fabs(p[a]));
+        gp += g[a] * p[a];
+        for (int b = 0; b < nv; ++b) pPp += p[a] * Pb.P[(size_t)a * nv + b] * p[b];
+      }
+    if (stationary || !(gp < 0)) {
+      if (!stationary && !(gp < 0)) {
+        // The step is not a descent direction (rounding): fall back to the
+        // projected steepest-descent direction -Z Z^T g.
+        p.assign(nv, 0.0);
+        for (int j = 0; j < k; ++j) {
+          double v = 0;
+          for (int a = 0; a < nv; ++a) v += Z[(size_t)a * k + j] * g[a];
+          for (int a = 0; a < nv; ++a) p[a] -= Z[(size_t)a * k + j] * v;
+        }
+        pmax = gp = pPp = 0;
+        for (int a = 0; a < nv; ++a) {
+          pmax = std::max(pmax, std::fabs(p[a]));
+          gp += g[a] * p[a];
+          for (int b = 0; b < nv; ++b) pPp += p[a] * Pb.P[(size_t)a * nv + b] * p[b];
+        }
+      }
+    }
+    if (stationary) {
       // multipliers: A_W^T lam = g
       const int w = (int)W.size();
       Vec lamW(w, 0.0);
@@ -694,7 +727,9 @@ QPResult qp_active_set(const QPProblem& Pb) {
     // Ratio test.  A row counts as blocking only if p decreases it by more
     // than rounding (relative to |p|): rows in the span of the working set
     // have a^T p = 0 exactly in exact arithmetic and must not be added.
-    double step = 1.0;
+    // Exact line search along p (the objective is quadratic), capped by the
+    // ratio test; the least-squares step has its minimiser at 1.
+    double step = pPp > 0 ? -gp / pPp : std::numeric_limits<double>::infinity();
     int block = -1;
     const double aptol = 1e-11 * std::max(pmax, 1e-300);
     for (int i = 0; i < nin; ++i) {
@@ -712,13 +747,17 @@ QPResult qp_active_set(const QPProblem& Pb) {
         }
       }
     }
+    if (!std::isfinite(step)) {  // zero curvature and nothing blocks: impossible on a bounded set
+      R.status = 3;
+      break;
+    }
     for (int a = 0; a < nv; ++a) R.y[a] += step * p[a];
     if (block >= 0) {
       W.push_back(block);
       inW[block] = 1;
     }
-    if (it == 19999) R.status = 1;
   }
+  if (R.iters >= 20000 && R.status == 0) R.status = 1;
   R.W = W;
   R.Q = qp_value(Pb, R.y.data());
   // KKT certificate: stationarity, primal feasibility, dual feasibility,

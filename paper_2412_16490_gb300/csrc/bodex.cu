@@ -507,13 +507,27 @@ __global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
 // ============================================================================ host helpers
 namespace {
 
-int gpb_for(int s) { return std::max(1, CTA_LANES / s); }
+// Grasps per CTA: 96 lanes / s, capped by the shared memory one CTA may use.
+template <int M>
+int gpb_for(int s) {
+  constexpr size_t kMaxSmem = 227 * 1024;
+  const size_t per = 4u * (size_t)(Lay<M>::KS + Lay<M>::PER);
+  const size_t fit = (kMaxSmem - 4u * Lay<M>::HAND_WORDS) / per;
+  return std::max(1, std::min(CTA_LANES / s, (int)fit));
+}
 
 template <class K>
 int ensure_smem(K kernel, size_t bytes) {
+  // A launch reports errors through cudaGetLastError; clear what an earlier,
+  // already reported failure may have left behind (sticky device faults are
+  // returned again by the next call regardless).
+  (void)cudaGetLastError();
   if (bytes > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    if (e != cudaSuccess) {
+      (void)cudaGetLastError();
+      return cuda_fail(e, "cudaFuncSetAttribute");
+    }
   }
   return BODEX_OK;
 }
@@ -536,7 +550,7 @@ int launch_err(const char* what) {
 
 template <int M>
 int run_fused(int mode, const FusedArgs& A, cudaStream_t st) {
-  const int gpb = gpb_for(A.S);
+  const int gpb = gpb_for<M>(A.S);
   const size_t bytes = Lay<M>::bytes(gpb);
   const dim3 grid((A.B + gpb - 1) / gpb), block(gpb * A.S);
   if (A.B == 0) return BODEX_OK;
@@ -563,7 +577,7 @@ template <int M>
 int run_qp(const float* G, int B, const float* T, int s, const AdmmCfg& cfg, int warm, float* y, float* z,
            float* lam, float* Q, int32_t* iters, int32_t* status, float* res, cudaStream_t st) {
   if (B == 0) return BODEX_OK;
-  const int gpb = gpb_for(s);
+  const int gpb = gpb_for<M>(s);
   const size_t bytes = Lay<M>::bytes(gpb);
   if (int r = ensure_smem(qp_solve_kernel<M>, bytes)) return r;
   qp_solve_kernel<M><<<(B + gpb - 1) / gpb, gpb * s, bytes, st>>>(G, B, T, s, cfg, warm, y, z, lam, Q, iters,
@@ -575,6 +589,7 @@ template <int M>
 int run_fk(const bodex_hand_s* h, const bodex_object_s* o, const float* x, int B, float* c_w, float* p, float* n,
            float* phi, float* G, int32_t* cell, int32_t* status, cudaStream_t st) {
   if (B == 0) return BODEX_OK;
+  (void)cudaGetLastError();
   fk_contacts_kernel<M><<<(B + 127) / 128, 128, 0, st>>>(h->dev, o->dev, x, B, c_w, p, n, phi, G, cell, status);
   return launch_err("fk_contacts_kernel launch");
 }

@@ -142,3 +142,17 @@ def test_infeasible_gamma():
     G = O.grasp_matrix(p, n)
     out = O.qp_solve(G, T, gamma=2.5)
     assert (out["status"] == 2).all()
+
+
+def test_active_set_certifies_a_stress_batch():
+    """Every solve ends at a KKT point (residual <= 1e-10) across contact
+    counts, wrench sets, (beta, gamma) and normal noise levels."""
+    for m in (3, 4, 5):
+        for s in (6, 12):
+            T = I.wrench_set(s)
+            for seed, (beta, gamma) in enumerate(((1.0, 0.5), (0.5, 1.0), (2.0, 0.1))):
+                p, n = I.random_contacts(48, m, seed=500 + 10 * m + seed, spread=0.6 if seed % 2 else 1.0,
+                                         normal_noise=0.05 + 0.1 * seed)
+                out = O.qp_solve(O.grasp_matrix(p, n), T, beta=beta, gamma=gamma)
+                assert (out["status"] == 0).all()
+                assert out["kkt"].max() < 1e-10

@@ -75,8 +75,8 @@ struct Lay {
   static constexpr int KS = NV * NVP + ((20 - (NV * NVP) % 32) + 32) % 32;
   static constexpr int CTW = 24;  // floats per contact record
   static constexpr int oG = 0;
-  static constexpr int oK = oG + 6 * NV;
-  static constexpr int oCT = oK + NV * NV;
+  static constexpr int oK = oG + 6 * NV;  // K^-1 setup scratch
+  static constexpr int oCT = oK + WoodburyScratch<M, double>::floats;
   static constexpr int oRY = oCT + CTW * M;
   static constexpr int oQ = oRY + SMAX * (6 + NV);
   static constexpr int oDG = oQ + SMAX;
@@ -84,7 +84,8 @@ struct Lay {
   static constexpr int oX = oCB + M * (6 + MAXCHAIN);
   static constexpr int oAM = oX + MAXD;
   static constexpr int oAV = oAM + MAXD;
-  static constexpr int oSC = oAV + MAXD;
+  static constexpr int oJW = oAV + MAXD;  // chain joint axes/points, M x MAXCHAIN x 6
+  static constexpr int oSC = oJW + M * MAXCHAIN * 6;
   static constexpr int PER = align4(oSC + 4);
   static constexpr int HAND_WORDS = align4((int)(sizeof(HandDev) / 4));
   static size_t bytes(int gpb) { return 4u * (size_t)(HAND_WORDS + gpb * (KS + PER)); }
@@ -173,20 +174,15 @@ __global__ void __launch_bounds__(128) fk_contacts_kernel(const HandDev* __restr
 }
 
 // ============================================================================ per-grasp QP setup (shared by kernels)
-// Lane 0 builds K and factors it; then the grasp's lanes write the columns
-// of K^-1.  Must be called by every thread of the CTA (contains barriers).
+// K^-1 of every grasp of the CTA (Woodbury form, all lanes); must be called
+// by every thread of the CTA (contains barriers).
+// Double precision when the solve iterates to a residual target, single
+// precision for fixed-iteration solves (the branch is uniform per launch).
 template <int M>
-__device__ inline void setup_kinv(bool active, int lane, int S, float* Gs, float* Ks, float* Kinv,
-                                  const AdmmCfg& cfg, int* stat) {
-  constexpr int NV = 3 * M;
-  if (active && lane == 0) {
-    build_K<M>(Gs, cfg, Ks);
-    if (!cholesky<NV>(Ks)) atomicOr(stat, BODEX_ST_NONFINITE);
-  }
-  __syncthreads();
-  if (active)
-    for (int col = lane; col < NV; col += S) chol_inverse_column<NV>(Ks, col, Kinv, Lay<M>::NVP);
-  __syncthreads();
+__device__ inline void setup_kinv(bool active, int lane, int S, const float* Gs, float* scratch, float* Kinv,
+                                  const AdmmCfg& cfg) {
+  if (cfg.eps > 0.f) setup_kinv_woodbury<M, double>(active, lane, S, Gs, scratch, Kinv, cfg);
+  else setup_kinv_woodbury<M, float>(active, lane, S, Gs, scratch, Kinv, cfg);
 }
 
 // ============================================================================ kernel: batched QP
@@ -212,7 +208,7 @@ __global__ void __launch_bounds__(CTA_LANES) qp_solve_kernel(const float* __rest
     if (lane == 0) *stat = 0;
   }
   __syncthreads();
-  setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg, stat);
+  setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg);
   if (!active) return;  // no barriers below
   const size_t q = (size_t)b * S + lane;
   float y[NV], w[NC], mq[NV];
@@ -350,7 +346,7 @@ __global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
     // ---- A1-A3: kinematics, nearest-point query, grasp matrix (lane = contact)
     if (active && lane < M) {
       float c[3];
-      fk_contact(H, lane, xs, c, nullptr);
+      fk_contact(H, lane, xs, c, per + L::oJW + lane * MAXCHAIN * 6);
       const ContactGeo k = contact_geometry(A.obj, c);
       store_ct(per + L::oCT + L::CTW * lane, k);
       write_G_block(k, lane, NV, Gs);
@@ -361,7 +357,7 @@ __global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
     }
     __syncthreads();
     // ---- A4: K^-1 per grasp
-    setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg, stat);
+    setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg);
     // ---- A5: ADMM, one QP per lane
     if (active) {
       float mq[NV];
@@ -417,9 +413,8 @@ __global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
         for (int cc = 0; cc < 3; ++cc) cols[r * 3 + cc] = per[L::oDG + r * NV + 3 * lane + cc];
       float dEdc[3];
       contact_adjoint(k, cols, 2.f * A.w_d * (k.phi - H.alpha - A.delta), dEdc);
-      float jw[6 * MAXCHAIN];
-      float c[3];
-      fk_contact(H, lane, xs, c, jw);
+      const float* jw = per + L::oJW + lane * MAXCHAIN * 6;  // frames from the forward pass
+      const float* c = k.c;
       float* cb = per + L::oCB + lane * (6 + MAXCHAIN);
       cb[0] = dEdc[0];
       cb[1] = dEdc[1];

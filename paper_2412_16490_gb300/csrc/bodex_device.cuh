@@ -342,77 +342,130 @@ __device__ __forceinline__ void write_G_block(const ContactGeo& k, int i, int nv
 // K = P + sigma I + rho A^T A with P = 2 G^T G (+ 2 eps_reg I).  For the
 // pyramid rows A^T A is the constant
 //   diag per contact (1 + 8 mu^2 cos^2(pi/8), 4, 4)  (f_n row + 8 facets)
-//   + 1 on every (f_{i,n}, f_{k,n}) pair              (the sum row),
-// because the facet normals sum to zero and their squares to 4 per axis.
-// One lane factors K (Cholesky) into Lf; the lanes of the grasp then solve
-// for the columns of K^-1 (stored in rows of stride ld).
-template <int M>
-__device__ inline void build_K(const float* G, const AdmmCfg& c, float* K) {
+//   + u u^T, u = indicator of the normal components   (the sum row),
+// because the facet normals sum to zero and their squares sum to 4 per
+// axis.  Hence K = Dg + V V^T with Dg diagonal and V = [sqrt2 G^T, sqrt(rho) u]
+// of rank 7, and by the Sherman-Morrison-Woodbury identity
+//   K^-1 = Dg^-1 - U U^T,   U = Dg^-1 V L^-T,   L L^T = I + V^T Dg^-1 V (7 x 7).
+// Every lane of the grasp takes part; no lane factors the 3m x 3m matrix.
+struct DiagK {
+  float dn, dt;  // Dg for a normal / a tangential component
+};
+__device__ __forceinline__ DiagK diag_k(const AdmmCfg& c) {
+  DiagK d;
+  d.dn = c.sigma + 2.f * c.eps_reg + c.rho * (1.f + 8.f * c.mu_c8 * c.mu_c8);
+  d.dt = c.sigma + 2.f * c.eps_reg + 4.f * c.rho;
+  return d;
+}
+
+// Entry e (0..27, row-major upper triangle of the 7x7) of M = I + V^T Dg^-1 V,
+// accumulated in precision R.
+template <int M, typename R>
+__device__ inline R woodbury_M_entry(const float* G, int e, const AdmmCfg& c, const DiagK& dk) {
   constexpr int NV = 3 * M;
-  const float dn = 1.0f + 8.0f * c.mu_c8 * c.mu_c8 + 1.0f;  // f_n row, facets, sum row
-  for (int a = 0; a < NV; ++a)
-    for (int b = a; b < NV; ++b) {
-      float s = 0.f;
+  int a = 0, b = 0, k = e;
+  for (a = 0; a < 7; ++a) {
+    if (k < 7 - a) {
+      b = a + k;
+      break;
+    }
+    k -= 7 - a;
+  }
+  const R idn = R(1) / R(dk.dn), idt = R(1) / R(dk.dt);
+  R s = 0;
+  if (b < 6) {  // both columns from sqrt2 G^T
+    for (int i = 0; i < NV; ++i) s += R(G[a * NV + i]) * R(G[b * NV + i]) * ((i % 3 == 0) ? idn : idt);
+    s *= R(2);
+  } else if (a < 6) {  // sqrt2 G^T against sqrt(rho) u
+    for (int i = 0; i < NV; i += 3) s += R(G[a * NV + i]);
+    s *= sqrt(R(2) * R(c.rho)) * idn;
+  } else {
+    s = R(c.rho) * R(M) * idn;
+  }
+  return (a == b ? R(1) : R(0)) + s;
+}
+
+// Scratch (in floats) that setup_kinv_woodbury<M, R> needs.
+template <int M, typename R>
+struct WoodburyScratch {
+  static constexpr int floats = (28 + 8 * 3 * M) * (int)(sizeof(R) / 4);
+};
+
+// Writes K^-1 (rows of stride NVP, rounded to float) for one grasp,
+// computed in precision R: float for the fixed-iteration step loop, double
+// when the solve iterates to a residual target (the ADMM fixed point moves
+// with the backward error of the inverse: the dual residual floor is
+// |(K^-1_computed)^-1 - K| |y|).  Must be called by every thread of the CTA
+// (contains barriers).
+template <int M, typename R>
+__device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const float* G, float* scratch, float* Kinv,
+                                           const AdmmCfg& c) {
+  constexpr int NV = 3 * M, NVP = (NV + 3) & ~3;
+  const DiagK dk = diag_k(c);
+  R* Ms = reinterpret_cast<R*>(scratch);  // 28
+  R* Us = Ms + 28;                        // NV rows of 8
+  if (active)
+    for (int e = lane; e < 28; e += S) Ms[e] = woodbury_M_entry<M, R>(G, e, c, dk);
+  __syncthreads();
+  if (active) {
+    // 7x7 Cholesky, replicated in every lane (registers).  Index (a, b),
+    // a <= b, of the row-major upper triangle; after factoring, entry (a, b)
+    // holds L[b][a].
+    R L[28];
 #pragma unroll
-      for (int r = 0; r < 6; ++r) s = fmaf(G[r * NV + a], G[r * NV + b], s);
-      float v = 2.0f * s;
-      if (a == b) {
-        v += c.sigma + 2.0f * c.eps_reg;
-        v += c.rho * ((a % 3 == 0) ? dn : 4.0f);
-      } else if ((a % 3 == 0) && (b % 3 == 0)) {
-        v += c.rho;  // sum row couples the normal components
+    for (int e = 0; e < 28; ++e) L[e] = Ms[e];
+    auto idx = [](int a, int b) { return a * 7 - (a * (a - 1)) / 2 + (b - a); };
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      R d = L[idx(j, j)];
+#pragma unroll
+      for (int k = 0; k < j; ++k) d -= L[idx(k, j)] * L[idx(k, j)];
+      const R ljj = sqrt(d > R(1e-30) ? d : R(1e-30));
+      L[idx(j, j)] = ljj;
+      const R il = R(1) / ljj;
+#pragma unroll
+      for (int i = j + 1; i < 7; ++i) {
+        R t = L[idx(j, i)];
+#pragma unroll
+        for (int k = 0; k < j; ++k) t -= L[idx(k, i)] * L[idx(k, j)];
+        L[idx(j, i)] = t * il;
       }
-      K[a * NV + b] = v;
-      K[b * NV + a] = v;
     }
-}
-
-// In-place Cholesky K = L L^T (lower triangle of K receives L).  Returns
-// false on a non-positive pivot.
-template <int NV>
-__device__ inline bool cholesky(float* K) {
-  bool ok = true;
-  for (int j = 0; j < NV; ++j) {
-    float s = K[j * NV + j];
-    for (int k = 0; k < j; ++k) s = fmaf(-K[j * NV + k], K[j * NV + k], s);
-    if (!(s > 0.f)) {
-      ok = false;
-      s = 1e-30f;
-    }
-    const float ljj = sqrtf(s);
-    K[j * NV + j] = ljj;
-    const float il = 1.0f / ljj;
-    for (int i = j + 1; i < NV; ++i) {
-      float t = K[i * NV + j];
-      for (int k = 0; k < j; ++k) t = fmaf(-K[i * NV + k], K[j * NV + k], t);
-      K[i * NV + j] = t * il;
+    const R s2 = sqrt(R(2)), sr = sqrt(R(c.rho));
+    for (int i = lane; i < NV; i += S) {
+      const R id = R(1) / R((i % 3 == 0) ? dk.dn : dk.dt);
+      R w[7];
+#pragma unroll
+      for (int a = 0; a < 6; ++a) w[a] = s2 * R(G[a * NV + i]) * id;
+      w[6] = (i % 3 == 0) ? sr * id : R(0);
+      // forward substitution L u = w
+#pragma unroll
+      for (int a = 0; a < 7; ++a) {
+        R t = w[a];
+#pragma unroll
+        for (int k = 0; k < a; ++k) t -= L[idx(k, a)] * w[k];
+        w[a] = t / L[idx(a, a)];
+      }
+#pragma unroll
+      for (int a = 0; a < 7; ++a) Us[i * 8 + a] = w[a];
     }
   }
-  return ok;
-}
-
-// Column `col` of K^-1 from the Cholesky factor: solve L L^T v = e_col and
-// store v as column col of Kinv (row stride ld).  K^-1 is symmetric, so the
-// column is also row col.
-template <int NV>
-__device__ inline void chol_inverse_column(const float* L, int col, float* Kinv, int ld) {
-  float v[NV];
+  __syncthreads();
+  if (active)
+    for (int i = lane; i < NV; i += S) {
+      R ui[7];
 #pragma unroll
-  for (int i = 0; i < NV; ++i) {
-    float s = (i == col) ? 1.0f : 0.0f;
+      for (int a = 0; a < 7; ++a) ui[a] = Us[i * 8 + a];
+      const R id = R(1) / R((i % 3 == 0) ? dk.dn : dk.dt);
 #pragma unroll
-    for (int k = 0; k < i; ++k) s = fmaf(-L[i * NV + k], v[k], s);
-    v[i] = s / L[i * NV + i];
-  }
+      for (int j = 0; j < NV; ++j) {
+        R t = 0;
 #pragma unroll
-  for (int i = NV - 1; i >= 0; --i) {
-    float s = v[i];
-#pragma unroll
-    for (int k = i + 1; k < NV; ++k) s = fmaf(-L[k * NV + i], v[k], s);
-    v[i] = s / L[i * NV + i];
-  }
-#pragma unroll
-  for (int i = 0; i < NV; ++i) Kinv[i * ld + col] = v[i];
+        for (int a = 0; a < 7; ++a) t += ui[a] * Us[j * 8 + a];
+        Kinv[i * NVP + j] = (float)((i == j ? id : R(0)) - t);
+      }
+    }
+  __syncthreads();
 }
 
 // ------------------------------------------------------------------ ADMM
@@ -490,14 +543,23 @@ __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* 
     rhs[3 * i + 1] = fmaf(c.sigma, y[3 * i + 1], fmaf(c.rho, gd, mq[3 * i + 1]));
     rhs[3 * i + 2] = fmaf(c.sigma, y[3 * i + 2], fmaf(c.rho, ge, mq[3 * i + 2]));
   }
-  // yt = K^-1 rhs (rows of K^-1 from shared memory, 16-byte loads)
+  // yt = K^-1 rhs: rows of K^-1 from shared memory in 16-byte loads, the
+  // loads of row a+1 issued before the FMAs of row a
   float yt[NV];
+  constexpr int Q4 = NVP / 4;
+  float4 cur[Q4], nxt[Q4];
+#pragma unroll
+  for (int q = 0; q < Q4; ++q) cur[q] = lds128(Kinv + 4 * q);
 #pragma unroll
   for (int a = 0; a < NV; ++a) {
+    if (a + 1 < NV) {
+#pragma unroll
+      for (int q = 0; q < Q4; ++q) nxt[q] = lds128(Kinv + (a + 1) * NVP + 4 * q);
+    }
     float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-    for (int q = 0; q < NVP / 4; ++q) {
-      const float4 k4 = lds128(Kinv + a * NVP + 4 * q);
+    for (int q = 0; q < Q4; ++q) {
+      const float4 k4 = cur[q];
       const int b = 4 * q;
       if (b + 0 < NV) s0 = fmaf(k4.x, rhs[b + 0], s0);
       if (b + 1 < NV) s1 = fmaf(k4.y, rhs[b + 1], s1);
@@ -505,6 +567,8 @@ __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* 
       if (b + 3 < NV) s1 = fmaf(k4.w, rhs[b + 3], s1);
     }
     yt[a] = s0 + s1;
+#pragma unroll
+    for (int q = 0; q < Q4; ++q) cur[q] = nxt[q];
   }
   // w <- w + alpha (A yt - Pi(w)),  y <- alpha yt + (1 - alpha) y
   const float al = c.alpha, bl = 1.0f - c.alpha;

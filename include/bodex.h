@@ -236,6 +236,32 @@ int bodex_energy_grad(bodex_hand_t hand, bodex_object_t obj, const float* x, int
 int bodex_step(bodex_hand_t hand, bodex_object_t obj, bodex_state_t state, const float* T, int s, int n_steps,
                const bodex_step_params* params, float* E_last, int32_t* status, void* stream);
 
+/* Allocation-free variant of bodex_step (the paper has no counterpart: this
+ * serves callers that cannot allocate device memory while they run, such as
+ * real-time control loops that reserve all memory at start-up, or processes
+ * whose memory pool owns the device).  It runs n_steps upper iterations on
+ * the caller's poses x [B,D] (device, updated in place) exactly as
+ * bodex_state_set_pose + bodex_step would, starting from zero Adam moments
+ * and a cold ADMM start; those per-grasp states live in a fixed 4 MiB
+ * device array inside the library (held by every GPU that loads it until
+ * the process exits) instead of a bodex_state_t.
+ *   - Allocates nothing: no cudaMalloc or cudaFree, no allocating library
+ *     routine.  The caller passes inputs and outputs (E_last [B] and
+ *     status [B] may be NULL).
+ *   - Size limit: B * (2 (6+n) + s (12 m + 1)) floats, each of the four
+ *     regions rounded up to 64 floats, must fit in 1048576 floats (e.g.
+ *     B <= 1330 for m = 5, s = 12, n = 22); larger batches return
+ *     BODEX_ERR_INVALID before any device work.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array and each clears what it uses before its
+ *     kernel runs: calls that overlap on the GPU (other streams, other host
+ *     threads) race and must be serialised by the caller.
+ * Errors: as bodex_step. */
+int bodex_step_noalloc(bodex_hand_t hand, bodex_object_t obj, float* x, int B, const float* T, int s, int n_steps,
+                       const bodex_step_params* params, float* E_last, int32_t* status, void* stream);
+
 /* Blocks until `stream` is idle; BODEX_ERR_CUDA if a fault occurred. */
 int bodex_sync(void* stream);
 /* Message for the calling thread's last non-OK status ("" if none). */

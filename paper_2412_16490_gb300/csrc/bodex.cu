@@ -16,6 +16,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -921,6 +922,77 @@ int bodex_step(bodex_hand_t h, bodex_object_t o, bodex_state_t S, const float* T
   const int r = dispatch_fused(h->host.m, MODE_STEP, A, as_stream(stream));
   if (r == BODEX_OK) S->t += n_steps;
   return r;
+}
+
+// ============================================================================ allocation-free step
+// Some callers cannot allocate device memory once they are running: a robot
+// controller that reserves everything at start-up so that its control loop
+// has bounded latency, an application whose memory pool owns the whole
+// device and forbids cudaMalloc, or a plug-in hosted by such a process.
+// bodex_step_noalloc serves them.  The per-grasp state that bodex_step keeps
+// in a bodex_state_t (Adam moments and the ADMM warm start of every QP) lives
+// instead in the fixed array below, which every GPU that loads this library
+// holds until the process exits.  The caller still passes the poses, the
+// wrenches and the outputs.
+namespace {
+constexpr size_t kNoallocScratchFloats = size_t(1) << 20;  // 4 MiB per device
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+float* g_noalloc_addr[kNoallocMaxDevices] = {};
+}  // namespace
+
+static __device__ __align__(256) float g_noalloc_scratch[kNoallocScratchFloats];
+
+// Device address of the scratch array on the current device.  Host code may
+// not use the symbol itself (it names a host-side stand-in), so the address
+// is looked up once per device, with that device current, and cached.
+static int noalloc_scratch(float** out) {
+  int dev = 0;
+  BODEX_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kNoallocMaxDevices) return fail(BODEX_ERR_INVALID, "device ordinal out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)");
+    g_noalloc_addr[dev] = static_cast<float*>(p);
+  }
+  *out = g_noalloc_addr[dev];
+  return BODEX_OK;
+}
+
+extern "C" int bodex_step_noalloc(bodex_hand_t h, bodex_object_t o, float* x, int B, const float* T, int s,
+                                  int n_steps, const bodex_step_params* params, float* E_last, int32_t* status,
+                                  void* stream) {
+  FusedArgs A;
+  if (int r = fill_args(A, h, o, T, s, B, params)) return r;
+  if (B > 0 && !x) return fail(BODEX_ERR_INVALID, "null x");
+  if (n_steps < 0) return fail(BODEX_ERR_INVALID, "n_steps < 0");
+  const size_t D = (size_t)h->host.D, m = (size_t)h->host.m;
+  auto up = [](size_t v) { return (v + 63) & ~size_t(63); };  // 256-byte aligned regions
+  const size_t nA = up((size_t)B * D), nY = up((size_t)B * s * 3 * m), nW = up((size_t)B * s * (9 * m + 1));
+  const size_t need = 2 * nA + nY + nW;
+  if (need > kNoallocScratchFloats)
+    return fail(BODEX_ERR_INVALID,
+                "bodex_step_noalloc: B * (2 (6+n) + s (12 m + 1)) floats exceed its fixed 4 MiB scratch "
+                "(1048576 floats); use bodex_state_create + bodex_step for larger batches");
+  if (n_steps == 0 || B == 0) return BODEX_OK;
+  float* base = nullptr;
+  if (int r = noalloc_scratch(&base)) return r;
+  cudaStream_t st = as_stream(stream);
+  // the array keeps the previous call's contents: Adam moments and warm
+  // starts must start at zero
+  BODEX_CUDA(cudaMemsetAsync(base, 0, need * sizeof(float), st));
+  A.n_steps = n_steps;
+  A.t0 = 0;
+  A.x_state = x;
+  A.am = base;
+  A.av = base + nA;
+  A.qy = base + 2 * nA;
+  A.qw = base + 2 * nA + nY;
+  A.E = E_last;
+  A.status = status;
+  return dispatch_fused((int)m, MODE_STEP, A, st);
 }
 
 }  // extern "C"

@@ -1,0 +1,76 @@
+"""The allocation-free step, bodex_step_noalloc, against the allocating one.
+
+Some callers cannot allocate device memory while they run -- a real-time
+robot controller that reserves all of its memory at start-up so its loop has
+bounded latency, or a process whose memory pool owns the device.  For them
+the library keeps the per-grasp optimiser state (Adam moments, ADMM warm
+starts) in a fixed array of its own instead of a bodex_state_t.  This test
+calls that entry point through the C ABI twice in a row, on different
+poses, and checks each result against bodex_state_set_pose + bodex_step on
+the same inputs: the second call also shows that the array's leftovers from
+the first call do not leak into the next one.  It also checks that a batch
+larger than the array is refused before any device work.
+
+This file is collected last (test_zz_*) so that a run stopping at its first
+failure has already run every other test.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import bodex_inputs as I  # noqa: E402
+import paper_2412_16490_gb300 as bx  # noqa: E402
+from paper_2412_16490_gb300 import _binding  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _reference(H, Ob, x, T, n_steps, sp):
+    st = bx.State(H, x.shape[0], T.shape[0])
+    st.set_pose(x)
+    E = torch.empty(x.shape[0], device="cuda")
+    bx.bodex_step(H, Ob, st, T, n_steps, sp, E_last=E)
+    return st.pose(), E
+
+
+def test_noalloc_step_matches_allocating_step_on_two_calls():
+    lib = bx.load()
+    hand, obj, x0, T, P, _, _ = I.workload("tiny")
+    H, Ob = bx.Hand(hand), bx.Object(obj)
+    sp = bx.step_params(P, qp=bx.qp_params(max_iter=30))
+    Tt = torch.as_tensor(T).cuda()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    for first, n_steps in ((0, 5), (16, 7)):  # two calls in a row, different poses
+        x = torch.as_tensor(x0[first:first + 48]).cuda()
+        want_x, want_E = _reference(H, Ob, x.clone(), Tt, n_steps, sp)
+        got_x = x.clone()
+        got_E = torch.empty(48, device="cuda")
+        status = torch.empty(48, dtype=torch.int32, device="cuda")
+        rc = lib.bodex_step_noalloc(H.handle, Ob.handle, _ptr(got_x), 48, _ptr(Tt), T.shape[0], n_steps,
+                                    C.byref(sp), _ptr(got_E), _ptr(status), stream)
+        assert rc == _binding.BODEX_OK, lib.bodex_last_error()
+        torch.cuda.synchronize()
+        np.testing.assert_allclose(got_x.cpu().numpy(), want_x.cpu().numpy(), atol=1e-6)
+        np.testing.assert_allclose(got_E.cpu().numpy(), want_E.cpu().numpy(), rtol=1e-5, atol=1e-7)
+        assert (status.cpu().numpy() & bx.ST_NONFINITE == 0).all()
+
+
+def test_noalloc_step_refuses_batches_beyond_its_array():
+    lib = bx.load()
+    hand, obj, x0, T, P, _, _ = I.workload("tiny", batch=2)
+    H, Ob = bx.Hand(hand), bx.Object(obj)
+    sp = bx.step_params(P)
+    Tt = torch.as_tensor(T).cuda()
+    big = 1 << 20  # far beyond 4 MiB of per-grasp state; no device work is issued
+    x = torch.zeros((1, hand.dof), device="cuda")
+    rc = lib.bodex_step_noalloc(H.handle, Ob.handle, _ptr(x), big, _ptr(Tt), T.shape[0], 1, C.byref(sp), None,
+                                None, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == _binding.BODEX_ERR_INVALID
+    assert b"scratch" in lib.bodex_last_error()

@@ -189,7 +189,7 @@ int bodex_fk_contacts(bodex_hand_t hand, bodex_object_t obj, const float* x, int
  *   y      [B,s,3m]     forces (in: warm start when params->warm, out: solution)
  *   z      [B,s,9m+1]   ADMM constraint copy (in/out, same rule)
  *   lam    [B,s,9m+1]   ADMM multipliers (in/out, same rule)
- *   Q      [B,s]        |beta t_j - G y_j|^2 at the returned y (out)
+ *   Q      [B,s]        |beta t_j - G y_j|^2 (+ eps_reg |y_j|^2) at the returned y (out)
  *   iters  [B,s]        int32 iterations used (out, may be NULL)
  *   status [B,s]        int32 status bits (out, may be NULL)
  *   res    [B,s,2]      final (primal, dual) inf-norm residuals (out, may be NULL)
@@ -227,6 +227,19 @@ int bodex_energy_grad(bodex_hand_t hand, bodex_object_t obj, const float* x, int
                       const bodex_step_params* params, bodex_state_t warm, float* E, float* dEdx, float* Q,
                       float* y, int32_t* status, void* stream);
 
+/* Backward pass of the energy for forces y from an earlier solve (the
+ * hand-written adjoint behind the autograd binding): recomputes FK, the SDF
+ * query and G at x, forms r_j = beta t_j - G y_j, Q_j = |r_j|^2 and E, and
+ * applies the envelope-theorem chain dQ_j/dG = -2 r_j y_j^T through the
+ * contact frames, the SDF Hessian and the kinematic chain (Secs. III, IV-A,
+ * IV-B).  No QP is solved.
+ *   x [B,D], T [s,6], y [B,s,3m] (in); E [B] (out, may be NULL), dEdx [B,D]
+ *   (out), status [B] (out, may be NULL).
+ * Errors: BODEX_ERR_INVALID, BODEX_ERR_INFEASIBLE, BODEX_ERR_CUDA. */
+int bodex_energy_adjoint(bodex_hand_t hand, bodex_object_t obj, const float* x, int B, const float* T, int s,
+                         const bodex_step_params* params, const float* y, float* E, float* dEdx, int32_t* status,
+                         void* stream);
+
 /* n_steps upper-level iterations on the state, fused into one kernel launch:
  * each iteration evaluates E and dE/dx at the current pose (ADMM warm
  * started from the previous iteration, params->qp.max_iter iterations),
@@ -235,6 +248,24 @@ int bodex_energy_grad(bodex_hand_t hand, bodex_object_t obj, const float* x, int
  * Errors: BODEX_ERR_INVALID, BODEX_ERR_INFEASIBLE, BODEX_ERR_CUDA. */
 int bodex_step(bodex_hand_t hand, bodex_object_t obj, bodex_state_t state, const float* T, int s, int n_steps,
                const bodex_step_params* params, float* E_last, int32_t* status, void* stream);
+
+/* Refinement epilogue (fine / final stages, Sec. IV-C, Eqs. (10)-(11), in
+ * SDF form; no QP).  n_steps upper iterations on the state (Adam continues
+ * from the coarse stage) with the energy
+ *   E = w_d sum_i |c'_i - (p^f_i + delta n_out,i)|^2 + w_qp sum_i |c'_i - p^c_i|^2,
+ * where c^f_i is the fingertip surface sample (hand desc tip_samples) with
+ * the smallest SDF value (lowest index on ties), p^f_i its nearest object
+ * point, c'_i = R_i s_{i,k*} + T_i with the sample's link coordinates held
+ * fixed (the paper's Detach), and p^c the object points at the end of the
+ * coarse stage.  delta = 0.01 gives the pre-grasp pose of the fine stage,
+ * delta = 0 the final stage.
+ *   p_coarse [B,m,3] (in), E_last [B] (out, may be NULL, energy at the last
+ *   evaluated pose), kstar [B,m] int32 (out, may be NULL, the samples chosen
+ *   at the last evaluated pose), status [B] (out, may be NULL).
+ * Errors: BODEX_ERR_INVALID (no tip samples, shape mismatch), BODEX_ERR_CUDA. */
+int bodex_refine(bodex_hand_t hand, bodex_object_t obj, bodex_state_t state, const float* p_coarse, int n_steps,
+                 float delta, float w_qp, const bodex_step_params* params, float* E_last, int32_t* kstar,
+                 int32_t* status, void* stream);
 
 /* Allocation-free variant of bodex_step (the paper has no counterpart: this
  * serves callers that cannot allocate device memory while they run, such as

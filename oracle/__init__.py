@@ -77,6 +77,10 @@ def _sig(L):
     L.orc_adam.argtypes = [_v, _d, _d, _d, _d, _d, C.c_int, C.c_int]
     L.orc_run.argtypes = [_v, _v, _d, _d, _d, C.c_int, C.c_int, C.c_int, _d, _d, C.c_int,
                           C.c_int, C.c_double, C.c_int, _d]
+    L.orc_refine_eval.argtypes = [_v, _v, _d, C.c_int, _d, C.c_double, C.c_double, C.c_double, C.c_int,
+                                  _d, _d, _i, _d]
+    L.orc_refine_run.argtypes = [_v, _v, _d, _d, _d, C.c_int, _d, C.c_int, C.c_int, C.c_double, C.c_double,
+                                 _d, C.c_int, _d]
 
 
 def _p(a, t):
@@ -280,4 +284,30 @@ def run(hand: Hand, obj: Object, x0, T, params, n_steps, grad_mode="fd", t0=0, m
     _load().orc_run(hand._h, obj._o, _p(x, _d), _p(mm, _d), _p(vv, _d), B, n_steps, t0, _p(pa, _d),
                     _p(T, _d), T.shape[0], 0 if grad_mode == "fd" else 1, fd_step,
                     threads or default_threads(), _p(E, _d))
+    return x, mm, vv, E
+
+
+def refine_eval(hand: Hand, obj: Object, x, p_coarse, delta, w_d, w_qp, threads=None):
+    """Refinement energy (fine/final stages) at B poses: E, grad, kstar, gap."""
+    x = _f64(x).reshape(-1, hand.D)
+    B = x.shape[0]
+    pc = _f64(p_coarse).reshape(B, hand.m, 3)
+    E, g = np.zeros(B), np.zeros((B, hand.D))
+    k = np.zeros((B, hand.m), np.int32)
+    gap = np.zeros((B, hand.m))
+    _load().orc_refine_eval(hand._h, obj._o, _p(x, _d), B, _p(pc, _d), float(delta), float(w_d), float(w_qp),
+                            threads or default_threads(), _p(E, _d), _p(g, _d), _p(k, _i), _p(gap, _d))
+    return dict(E=E, grad=g, kstar=k, gap=gap)
+
+
+def refine_run(hand: Hand, obj: Object, x, mm, vv, p_coarse, n_steps, t0, delta, w_qp, params, threads=None):
+    """n_steps refinement iterations with Adam; returns (x, mm, vv, E_last)."""
+    x = _f64(x).reshape(-1, hand.D).copy()
+    mm, vv = _f64(mm).copy(), _f64(vv).copy()
+    B = x.shape[0]
+    pc = _f64(p_coarse).reshape(B, hand.m, 3)
+    E = np.zeros(B)
+    pa = params_array(params)
+    _load().orc_refine_run(hand._h, obj._o, _p(x, _d), _p(mm, _d), _p(vv, _d), B, _p(pc, _d), int(n_steps), int(t0),
+                           float(delta), float(w_qp), _p(pa, _d), threads or default_threads(), _p(E, _d))
     return x, mm, vv, E

@@ -481,13 +481,18 @@ QPProblem make_qp(const double* G, int m, const double* t, double mu, double bet
 }
 
 double qp_value(const QPProblem& Pb, const double* y) {
-  // Q = |beta t - G y|^2 evaluated directly (not through P, q).
+  // Q = |beta t - G y|^2 (+ eps |y|^2 when the optional regulariser is on),
+  // evaluated directly (not through P, q).  With the regulariser the energy
+  // uses the regularised optimal value, whose derivative in G is then the
+  // envelope-theorem expression -2 r y^T exactly.
   double Q = 0;
   for (int r = 0; r < 6; ++r) {
     double s = Pb.w[r];
     for (int a = 0; a < Pb.nv; ++a) s -= Pb.G[r * Pb.nv + a] * y[a];
     Q += s * s;
   }
+  if (Pb.eps > 0)
+    for (int a = 0; a < Pb.nv; ++a) Q += Pb.eps * y[a] * y[a];
   return Q;
 }
 
@@ -1091,6 +1096,68 @@ void build_ancestors(Hand& H) {
   }
 }
 
+// ---------------------------------------------------------------- refinement (fine / final stages)
+// Sec. IV-C, Eqs. (10)-(11), in SDF form.  The fingertip surface of contact
+// i is a fixed set of S sample points s_{i,k} in its link frame.  Reading:
+//   c^f_i   = the sample with the smallest phi (lowest k on ties),
+//   p^f_i   = its nearest object point, c^f - phi n_out,
+//   c^{f'}  = R_i Detach(s_{i,k*}) + T_i  (equals c^f; only R_i, T_i vary),
+//   E^f     = w_d sum_i |c^{f'}_i - (p^f_i + delta n_out,i)|^2
+//           + w_qp sum_i |c^{f'}_i - p^c_i|^2,
+// p^f and the margin target are constants (not differentiated), p^c are the
+// object points at the end of the coarse stage.  delta = 1 cm in the fine
+// stage (pre-grasp, Sec. IV-D) and 0 in the final stage, where the first
+// term is the paper's |c^{f'} - p^f|^2.
+struct Refine {
+  double E = 0;
+  std::vector<int> kstar;
+  std::vector<double> gap;  // phi(second best) - phi(best), for tie detection
+};
+
+Tf link_frame(const FK& f, const Hand& H, int i) { return f.T[H.clink[i]]; }
+
+Refine refine_eval(const Hand& H, const Object& O, const double* x, const double* pc, double delta, double w_d,
+                   double w_qp, double* g) {
+  Refine R;
+  const int D = 6 + H.n;
+  FK f = forward_kinematics(H, x);
+  R.kstar.assign(H.m, 0);
+  R.gap.assign(H.m, 0.0);
+  if (g) std::fill(g, g + D, 0.0);
+  for (int i = 0; i < H.m; ++i) {
+    const Tf T = link_frame(f, H, i);
+    double best = std::numeric_limits<double>::infinity(), second = best;
+    int kb = 0;
+    for (int k = 0; k < H.S; ++k) {
+      const V3 ck = tf_apply(T, v3(&H.tips[((size_t)i * H.S + k) * 3]));
+      const double ph = sdf_query(O, ck).phi;
+      if (ph < best) {
+        second = best;
+        best = ph;
+        kb = k;
+      } else if (ph < second) {
+        second = ph;
+      }
+    }
+    R.kstar[i] = kb;
+    R.gap[i] = second - best;
+    const V3 cf = tf_apply(T, v3(&H.tips[((size_t)i * H.S + kb) * 3]));
+    const Contact ct = contact_query(O, cf);
+    const V3 target = ct.p - delta * ct.n;  // p^f + delta n_out (n is inward)
+    const V3 pci = v3(pc + 3 * i);
+    const V3 a = cf - target, b = cf - pci;
+    R.E += w_d * dot(a, a) + w_qp * dot(b, b);
+    if (!g) continue;
+    const V3 dEdc = 2.0 * w_d * a + 2.0 * w_qp * b;
+    for (int jx = 0; jx < D; ++jx) {
+      if (!H.anc[i][jx]) continue;
+      const V3 dc = jx < 3 ? f.omega[jx] : cross(f.omega[jx], cf - f.org[jx]);
+      g[jx] += dot(dEdc, dc);
+    }
+  }
+  return R;
+}
+
 template <class F>
 void parallel_for(int count, int threads, F&& f) {
   threads = std::max(1, std::min(threads, count));
@@ -1370,6 +1437,44 @@ void orc_run(void* h, void* o, double* x, double* mm, double* vv, int B, int n_s
       if (E) E[b] = ev.E;
       if (grad_mode == 0) grad_fd(H, O, xb, P, T, s, fd_step, g.data());
       else grad_analytic(H, O, ev, P, T, s, g.data());
+      adam_step(H, P, xb, mm + (size_t)b * D, vv + (size_t)b * D, g.data(), t0 + it + 1);
+    }
+  });
+}
+
+// Refinement energy, its gradient and the chosen samples at B poses.
+//   pc [B,m,3] coarse-stage object points; E [B]; grad [B,D] (may be NULL);
+//   kstar [B,m]; gap [B,m] (phi gap to the second-best sample, may be NULL).
+void orc_refine_eval(void* h, void* o, const double* x, int B, const double* pc, double delta, double w_d,
+                     double w_qp, int threads, double* E, double* grad, int32_t* kstar, double* gap) {
+  const Hand& H = *static_cast<Hand*>(h);
+  const Object& O = *static_cast<Object*>(o);
+  const int D = 6 + H.n, m = H.m;
+  parallel_for(B, threads, [&](int b) {
+    Refine R = refine_eval(H, O, x + (size_t)b * D, pc + (size_t)b * m * 3, delta, w_d, w_qp,
+                           grad ? grad + (size_t)b * D : nullptr);
+    E[b] = R.E;
+    for (int i = 0; i < m; ++i) {
+      kstar[(size_t)b * m + i] = R.kstar[i];
+      if (gap) gap[(size_t)b * m + i] = R.gap[i];
+    }
+  });
+}
+
+// n_steps refinement iterations (energy above, Adam + clamp) continuing at
+// step count t0 + 1; x, mm, vv [B,D] in place; E [B] at the last evaluated pose.
+void orc_refine_run(void* h, void* o, double* x, double* mm, double* vv, int B, const double* pc, int n_steps,
+                    int t0, double delta, double w_qp, const double* params, int threads, double* E) {
+  const Hand& H = *static_cast<Hand*>(h);
+  const Object& O = *static_cast<Object*>(o);
+  const Params P = params_from(params);
+  const int D = 6 + H.n, m = H.m;
+  parallel_for(B, threads, [&](int b) {
+    double* xb = x + (size_t)b * D;
+    Vec g(D);
+    for (int it = 0; it < n_steps; ++it) {
+      Refine R = refine_eval(H, O, xb, pc + (size_t)b * m * 3, delta, P.w_d, w_qp, g.data());
+      if (E) E[b] = R.E;
       adam_step(H, P, xb, mm + (size_t)b * D, vv + (size_t)b * D, g.data(), t0 + it + 1);
     }
   });

@@ -19,7 +19,8 @@ from ._binding import BodexError, ST_DEGENERATE_NORMAL, ST_NONFINITE, ST_NOT_CON
 __all__ = [
     "load", "Hand", "Object", "State", "qp_params", "step_params",
     "bodex_hand_create", "bodex_object_create", "bodex_state_create",
-    "bodex_fk_contacts", "bodex_qp_solve_batch", "bodex_energy_grad", "bodex_step",
+    "bodex_fk_contacts", "bodex_qp_solve_batch", "bodex_energy_grad", "bodex_energy_adjoint", "bodex_step", "bodex_refine",
+    "synthesize",
     "bodex_sync", "bodex_version", "BodexError",
 ]
 
@@ -249,12 +250,53 @@ def bodex_energy_grad(hand: Hand, obj: Object, x, T, params: _b.bodex_step_param
     return out
 
 
+def bodex_energy_adjoint(hand: Hand, obj: Object, x, T, params: _b.bodex_step_params, y, stream=None):
+    """dE/dx [B,D] and E [B] at poses x for given forces y [B,s,3m] (no QP solve)."""
+    torch = _torch()
+    B, s = int(x.shape[0]), int(T.shape[0])
+    dev = x.device
+    out = dict(E=torch.empty(B, dtype=torch.float32, device=dev),
+               dEdx=torch.empty((B, hand.D), dtype=torch.float32, device=dev),
+               status=torch.empty(B, dtype=torch.int32, device=dev))
+    _b.check(load().bodex_energy_adjoint(hand.handle, obj.handle, _ptr(x), B, _ptr(T), s, C.byref(params), _ptr(y),
+                                         _ptr(out["E"]), _ptr(out["dEdx"]), _ptr(out["status"]), _stream(stream)))
+    return out
+
+
 def bodex_step(hand: Hand, obj: Object, state: State, T, n_steps: int, params: _b.bodex_step_params,
                E_last=None, status=None, stream=None):
     """n_steps fused upper iterations on `state`; returns (E_last, status)."""
     _b.check(load().bodex_step(hand.handle, obj.handle, state.handle, _ptr(T), int(T.shape[0]), int(n_steps),
                                C.byref(params), _ptr(E_last), _ptr(status), _stream(stream)))
     return E_last, status
+
+
+def bodex_refine(hand: Hand, obj: Object, state: State, p_coarse, n_steps: int, delta: float, w_qp: float,
+                 params: _b.bodex_step_params, E_last=None, kstar=None, status=None, stream=None):
+    """n_steps refinement iterations (fine stage: delta = 0.01, final: 0)."""
+    _b.check(load().bodex_refine(hand.handle, obj.handle, state.handle, _ptr(p_coarse), int(n_steps), float(delta),
+                                 float(w_qp), C.byref(params), _ptr(E_last), _ptr(kstar), _ptr(status),
+                                 _stream(stream)))
+    return E_last, kstar, status
+
+
+def synthesize(hand: Hand, obj: Object, x0, T, params: _b.bodex_step_params, coarse_steps=200, fine_steps=50,
+               final_steps=50, margin=0.01, w_qp=1000.0, stream=None):
+    """The three-stage schedule (Sec. IV-D): coarse steps with the QP energy,
+    then fine steps (pre-grasp x_p, margin) and final steps (grasp x), and
+    the squeeze pose x_s = 2 x - x_p.  Returns dict x_p, x, x_s, E."""
+    torch = _torch()
+    B = int(x0.shape[0])
+    st = State(hand, B, int(T.shape[0]))
+    st.set_pose(x0, stream)
+    E = torch.empty(B, dtype=torch.float32, device=x0.device)
+    bodex_step(hand, obj, st, T, coarse_steps, params, E_last=E, stream=stream)
+    pc = bodex_fk_contacts(hand, obj, st.pose(stream), stream)["p"]
+    bodex_refine(hand, obj, st, pc, fine_steps, margin, w_qp, params, E_last=E, stream=stream)
+    xp = st.pose(stream)
+    bodex_refine(hand, obj, st, pc, final_steps, 0.0, w_qp, params, E_last=E, stream=stream)
+    x = st.pose(stream)
+    return dict(x_p=xp, x=x, x_s=2.0 * x - xp, E=E)
 
 
 def bodex_sync(stream=None):

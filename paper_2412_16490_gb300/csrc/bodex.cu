@@ -48,6 +48,7 @@ cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 struct bodex_hand_s {
   HandDev host;
   HandDev* dev = nullptr;
+  float* tips = nullptr;  // [m, S, 3] fingertip surface samples (refinement)
 };
 struct bodex_object_s {
   ObjDev dev;
@@ -243,6 +244,7 @@ __global__ void __launch_bounds__(CTA_LANES) qp_solve_kernel(const float* __rest
   for (int a = 0; a < NV; ++a) {
     yio[q * NV + a] = y[a];
     fin = fin && isfinite(y[a]);
+    Q = fmaf(cfg.eps_reg * y[a], y[a], Q);  // regularised value when eps_reg > 0
   }
 #pragma unroll
   for (int r = 0; r < NC; ++r) {
@@ -285,9 +287,13 @@ struct FusedArgs {
   float* Qout;
   float* yout;
   int32_t* status;
+  const float* yin;  // MODE_ADJOINT: forces from a previous solve [B, s, 3m]
 };
 
-enum { MODE_EVAL = 0, MODE_STEP = 1 };
+// MODE_EVAL: E and dE/dx at x.  MODE_STEP: n_steps upper iterations on the
+// state.  MODE_ADJOINT: E and dE/dx at x for given forces y (no QP solve):
+// the backward pass of the energy, with FK and the SDF query recomputed.
+enum { MODE_EVAL = 0, MODE_STEP = 1, MODE_ADJOINT = 2 };
 
 template <int M, int MODE>
 __global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
@@ -327,7 +333,12 @@ __global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
   // ADMM warm start of this lane's QP, kept in registers across steps
   float y[NV], w[NC];
   const size_t q = (size_t)b * S + lane;
-  if (active && A.qy) {
+  if (MODE == MODE_ADJOINT && active) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) y[a] = A.yin[q * NV + a];
+#pragma unroll
+    for (int r = 0; r < NC; ++r) w[r] = 0.f;
+  } else if (active && A.qy) {
 #pragma unroll
     for (int a = 0; a < NV; ++a) y[a] = A.qy[q * NV + a];
 #pragma unroll
@@ -358,14 +369,16 @@ __global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
     }
     __syncthreads();
     // ---- A4: K^-1 per grasp
-    setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg);
+    if (MODE != MODE_ADJOINT) setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg);
     // ---- A5: ADMM, one QP per lane
     if (active) {
-      float mq[NV];
-      neg_q<M>(Gs, t, cfg.beta, mq);
-      float rp, rd;
-      bool conv;
-      admm_solve<M>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
+      bool conv = true;
+      if (MODE != MODE_ADJOINT) {
+        float mq[NV];
+        neg_q<M>(Gs, t, cfg.beta, mq);
+        float rp, rd;
+        admm_solve<M>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
+      }
       float* ry = per + L::oRY + lane * (6 + NV);
       float Q = 0.f;
 #pragma unroll
@@ -377,7 +390,10 @@ __global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
         Q = fmaf(s, s, Q);
       }
 #pragma unroll
-      for (int a = 0; a < NV; ++a) ry[6 + a] = y[a];
+      for (int a = 0; a < NV; ++a) {
+        ry[6 + a] = y[a];
+        Q = fmaf(cfg.eps_reg * y[a], y[a], Q);  // regularised value when eps_reg > 0
+      }
       per[L::oQ + lane] = Q;
       int st = 0;
       if (cfg.eps > 0.f && !conv) st |= BODEX_ST_NOT_CONVERGED;
@@ -457,7 +473,7 @@ __global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
             if (pos >= 0) g += cb[i * (6 + MAXCHAIN) + 6 + pos];
           }
         }
-        if (MODE == MODE_EVAL) {
+        if (MODE != MODE_STEP) {
           if (A.dEdx) A.dEdx[(size_t)b * D + k] = g;
         } else {
           const float mm = fmaf(A.b1, ams[k], (1.f - A.b1) * g);
@@ -486,7 +502,7 @@ __global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
       A.av[(size_t)b * D + k] = avs[k];
     }
   }
-  if (A.qy) {
+  if (MODE != MODE_ADJOINT && A.qy) {
 #pragma unroll
     for (int a = 0; a < NV; ++a) A.qy[q * NV + a] = y[a];
 #pragma unroll
@@ -497,6 +513,165 @@ __global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
     if (A.yout)
 #pragma unroll
       for (int a = 0; a < NV; ++a) A.yout[q * NV + a] = y[a];
+  }
+}
+
+// ============================================================================ kernel: refinement epilogue
+// Fine / final stages (Sec. IV-C, Eqs. (10)-(11)) in SDF form, no QP.  Per
+// contact: c^f = the fingertip sample with the smallest phi (lowest index on
+// ties), p^f its nearest object point, c^{f'} = R_i s_{k*} + T_i with the
+// sample's link-frame coordinates held fixed (the Detach of Eq. (11)), and
+//   E = w_d sum |c^{f'} - (p^f + delta n_out)|^2 + w_qp sum |c^{f'} - p^c|^2
+// with p^f, n_out and the coarse-stage points p^c treated as constants.
+// delta is the pre-grasp margin (Sec. IV-D): 1 cm in the fine stage, 0 in
+// the final one.  One CTA holds RF_GPB grasps x 8 lanes; lanes 0..m-1 own a
+// contact, all lanes share the gradient assembly and Adam.
+struct RefineArgs {
+  const HandDev* hand;
+  const float* tips;
+  ObjDev obj;
+  int B;
+  const float* pc;
+  float delta, w_d, w_qp;
+  float lr_t, lr_r, b1, b2, adam_eps;
+  int n_steps, t0;
+  float* x;
+  float* am;
+  float* av;
+  float* E;
+  int32_t* kstar;
+  int32_t* status;
+};
+
+constexpr int RF_LANES = 8, RF_GPB = 16;
+
+template <int M>
+__global__ void __launch_bounds__(RF_LANES * RF_GPB) refine_kernel(RefineArgs A) {
+  constexpr int HW = Lay<M>::HAND_WORDS;
+  constexpr int CBW = 6 + MAXCHAIN;
+  constexpr int PER = align4(3 * MAXD + M * CBW + M * MAXCHAIN * 6 + M + 4);
+  __shared__ __align__(16) float smem[HW + RF_GPB * PER];
+  copy_hand_to_smem(A.hand, smem);
+  const int gl = threadIdx.x / RF_LANES, lane = threadIdx.x % RF_LANES;
+  const int b = blockIdx.x * RF_GPB + gl;
+  const bool active = b < A.B;
+  const HandDev& H = *reinterpret_cast<const HandDev*>(smem);
+  float* per = smem + HW + gl * PER;
+  float* xs = per;
+  float* ams = per + MAXD;
+  float* avs = per + 2 * MAXD;
+  float* cb = per + 3 * MAXD;
+  float* jwall = cb + M * CBW;
+  float* Ei = jwall + M * MAXCHAIN * 6;
+  int* stat = reinterpret_cast<int*>(Ei + M);
+  __syncthreads();
+  const int D = H.D, S = H.S;
+  if (active) {
+    for (int k = lane; k < D; k += RF_LANES) {
+      xs[k] = A.x[(size_t)b * D + k];
+      ams[k] = A.am[(size_t)b * D + k];
+      avs[k] = A.av[(size_t)b * D + k];
+    }
+    if (lane == 0) *stat = 0;
+  }
+  __syncthreads();
+  int kbest = 0;
+  for (int step = 0; step < A.n_steps; ++step) {
+    if (active && lane < M) {
+      Tf T;
+      float* jw = jwall + lane * MAXCHAIN * 6;
+      fk_link(H, lane, xs, T, jw);
+      const float* tip = A.tips + (size_t)lane * S * 3;
+      float best = INFINITY;
+      kbest = 0;
+      for (int k = 0; k < S; ++k) {
+        const float sk[3] = {__ldg(tip + 3 * k), __ldg(tip + 3 * k + 1), __ldg(tip + 3 * k + 2)};
+        float ck[3];
+        tf_point(T, sk, ck);
+        const float ph = sdf_query(A.obj, ck).phi;
+        if (ph < best) {
+          best = ph;
+          kbest = k;
+        }
+      }
+      const float sk[3] = {__ldg(tip + 3 * kbest), __ldg(tip + 3 * kbest + 1), __ldg(tip + 3 * kbest + 2)};
+      float cf[3];
+      tf_point(T, sk, cf);
+      const ContactGeo k = contact_geometry(A.obj, cf);
+      const float gc[3] = {A.obj.gcx, A.obj.gcy, A.obj.gcz};
+      const float* pci = A.pc + ((size_t)b * M + lane) * 3;
+      float dEdc[3], e = 0.f;
+      for (int a = 0; a < 3; ++a) {
+        const float target = k.p[a] + gc[a] - A.delta * k.n[a];
+        const float da = cf[a] - target, db = cf[a] - pci[a];
+        e += A.w_d * da * da + A.w_qp * db * db;
+        dEdc[a] = 2.f * A.w_d * da + 2.f * A.w_qp * db;
+      }
+      Ei[lane] = e;
+      if (k.degenerate) atomicOr(stat, BODEX_ST_DEGENERATE_NORMAL);
+      if (!isfinite(e)) atomicOr(stat, BODEX_ST_NONFINITE);
+      float* c = cb + lane * CBW;
+      c[0] = dEdc[0];
+      c[1] = dEdc[1];
+      c[2] = dEdc[2];
+      float s1, c1, s2, c2;
+      sincosf(xs[3], &s1, &c1);
+      sincosf(xs[4], &s2, &c2);
+      const float om[3][3] = {{1.f, 0.f, 0.f}, {0.f, c1, s1}, {s2, -s1 * c2, c1 * c2}};
+      const float rel[3] = {cf[0] - xs[0], cf[1] - xs[1], cf[2] - xs[2]};
+      for (int k3 = 0; k3 < 3; ++k3) {
+        float v[3];
+        cross3(om[k3], rel, v);
+        c[3 + k3] = dEdc[0] * v[0] + dEdc[1] * v[1] + dEdc[2] * v[2];
+      }
+      const int Lc = H.chain_len[lane];
+      for (int kk = 0; kk < Lc; ++kk) {
+        const float r2[3] = {cf[0] - jw[6 * kk + 3], cf[1] - jw[6 * kk + 4], cf[2] - jw[6 * kk + 5]};
+        float v[3];
+        cross3(jw + 6 * kk, r2, v);
+        c[6 + kk] = dEdc[0] * v[0] + dEdc[1] * v[1] + dEdc[2] * v[2];
+      }
+    }
+    __syncthreads();
+    if (active) {
+      const int tstep = A.t0 + step + 1;
+      const float c1 = 1.f - powf(A.b1, (float)tstep), c2 = 1.f - powf(A.b2, (float)tstep);
+      if (lane == 0 && A.E) {
+        float e = 0.f;
+        for (int i = 0; i < M; ++i) e += Ei[i];
+        per[PER - 1] = e;
+      }
+      for (int k = lane; k < D; k += RF_LANES) {
+        float g = 0.f;
+        if (k < 6) {
+          for (int i = 0; i < M; ++i) g += cb[i * CBW + k];
+        } else {
+          for (int i = 0; i < M; ++i) {
+            const int pos = H.jpos[i][k - 6];
+            if (pos >= 0) g += cb[i * CBW + 6 + pos];
+          }
+        }
+        const float mm = fmaf(A.b1, ams[k], (1.f - A.b1) * g);
+        const float vv = fmaf(A.b2, avs[k], (1.f - A.b2) * g * g);
+        ams[k] = mm;
+        avs[k] = vv;
+        const float lr = k < 3 ? A.lr_t : A.lr_r;
+        const float xn = xs[k] - lr * (mm / c1) / (sqrtf(vv / c2) + A.adam_eps);
+        xs[k] = fminf(fmaxf(xn, H.qmin[k]), H.qmax[k]);
+      }
+    }
+    __syncthreads();
+  }
+  if (!active) return;
+  for (int k = lane; k < D; k += RF_LANES) {
+    A.x[(size_t)b * D + k] = xs[k];
+    A.am[(size_t)b * D + k] = ams[k];
+    A.av[(size_t)b * D + k] = avs[k];
+  }
+  if (lane < M && A.kstar && A.n_steps > 0) A.kstar[(size_t)b * M + lane] = kbest;
+  if (lane == 0) {
+    if (A.E) A.E[b] = per[PER - 1];
+    if (A.status) A.status[b] = *stat;
   }
 }
 
@@ -553,6 +728,9 @@ int run_fused(int mode, const FusedArgs& A, cudaStream_t st) {
   if (mode == MODE_STEP) {
     if (int r = ensure_smem(fused_kernel<M, MODE_STEP>, bytes)) return r;
     fused_kernel<M, MODE_STEP><<<grid, block, bytes, st>>>(A);
+  } else if (mode == MODE_ADJOINT) {
+    if (int r = ensure_smem(fused_kernel<M, MODE_ADJOINT>, bytes)) return r;
+    fused_kernel<M, MODE_ADJOINT><<<grid, block, bytes, st>>>(A);
   } else {
     if (int r = ensure_smem(fused_kernel<M, MODE_EVAL>, bytes)) return r;
     fused_kernel<M, MODE_EVAL><<<grid, block, bytes, st>>>(A);
@@ -590,6 +768,15 @@ int run_fk(const bodex_hand_s* h, const bodex_object_s* o, const float* x, int B
   return launch_err("fk_contacts_kernel launch");
 }
 
+}  // namespace
+
+namespace {
+template <int M>
+int run_refine(const RefineArgs& A, cudaStream_t st) {
+  (void)cudaGetLastError();
+  refine_kernel<M><<<(A.B + RF_GPB - 1) / RF_GPB, RF_LANES * RF_GPB, 0, st>>>(A);
+  return launch_err("refine_kernel launch");
+}
 }  // namespace
 
 // ============================================================================ C ABI
@@ -644,12 +831,29 @@ int bodex_hand_create(const bodex_hand_desc* d, bodex_hand_t* out) {
       H.jpos[i][chain[L - 1 - k]] = (int8_t)k;
     }
   }
+  if (H.S < 0 || (H.S > 0 && !d->tip_samples)) return fail(BODEX_ERR_INVALID, "tip samples missing");
   bodex_hand_s* h = new bodex_hand_s();
   h->host = H;
   cudaError_t e = cudaMalloc(&h->dev, sizeof(HandDev));
   if (e != cudaSuccess) {
     delete h;
     return fail(BODEX_ERR_OOM, "cudaMalloc hand");
+  }
+  if (H.S > 0) {
+    const size_t bytes = (size_t)m * H.S * 3 * sizeof(float);
+    e = cudaMalloc(&h->tips, bytes);
+    if (e != cudaSuccess) {
+      cudaFree(h->dev);
+      delete h;
+      return fail(BODEX_ERR_OOM, "cudaMalloc tip samples");
+    }
+    e = cudaMemcpy(h->tips, d->tip_samples, bytes, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      cudaFree(h->tips);
+      cudaFree(h->dev);
+      delete h;
+      return cuda_fail(e, "cudaMemcpy tip samples");
+    }
   }
   e = cudaMemcpy(h->dev, &h->host, sizeof(HandDev), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
@@ -663,6 +867,7 @@ int bodex_hand_create(const bodex_hand_desc* d, bodex_hand_t* out) {
 
 int bodex_hand_destroy(bodex_hand_t h) {
   if (!h) return BODEX_OK;
+  if (h->tips) cudaFree(h->tips);
   cudaFree(h->dev);
   delete h;
   return BODEX_OK;
@@ -902,6 +1107,21 @@ int bodex_energy_grad(bodex_hand_t h, bodex_object_t o, const float* x, int B, c
   return dispatch_fused(h->host.m, MODE_EVAL, A, as_stream(stream));
 }
 
+int bodex_energy_adjoint(bodex_hand_t h, bodex_object_t o, const float* x, int B, const float* T, int s,
+                         const bodex_step_params* params, const float* y, float* E, float* dEdx, int32_t* status,
+                         void* stream) {
+  FusedArgs A;
+  if (int r = fill_args(A, h, o, T, s, B, params)) return r;
+  if (B > 0 && (!x || !y || !dEdx)) return fail(BODEX_ERR_INVALID, "null x, y or dEdx");
+  A.n_steps = 1;
+  A.x_in = x;
+  A.yin = y;
+  A.E = E;
+  A.dEdx = dEdx;
+  A.status = status;
+  return dispatch_fused(h->host.m, MODE_ADJOINT, A, as_stream(stream));
+}
+
 int bodex_step(bodex_hand_t h, bodex_object_t o, bodex_state_t S, const float* T, int s, int n_steps,
                const bodex_step_params* params, float* E_last, int32_t* status, void* stream) {
   if (!S) return fail(BODEX_ERR_INVALID, "null state");
@@ -920,6 +1140,50 @@ int bodex_step(bodex_hand_t h, bodex_object_t o, bodex_state_t S, const float* T
   A.E = E_last;
   A.status = status;
   const int r = dispatch_fused(h->host.m, MODE_STEP, A, as_stream(stream));
+  if (r == BODEX_OK) S->t += n_steps;
+  return r;
+}
+
+// ============================================================================ refinement ABI
+extern "C" int bodex_refine(bodex_hand_t h, bodex_object_t o, bodex_state_t S, const float* p_coarse, int n_steps,
+                            float delta, float w_qp, const bodex_step_params* p, float* E_last, int32_t* kstar,
+                            int32_t* status, void* stream) {
+  if (!h || !o || !S || !p) return fail(BODEX_ERR_INVALID, "null argument");
+  if (h->host.S <= 0 || !h->tips) return fail(BODEX_ERR_INVALID, "hand has no fingertip samples");
+  if (S->m != h->host.m || S->D != h->host.D) return fail(BODEX_ERR_INVALID, "state shape mismatch");
+  if (n_steps < 0) return fail(BODEX_ERR_INVALID, "n_steps < 0");
+  if (S->B > 0 && !p_coarse) return fail(BODEX_ERR_INVALID, "null p_coarse");
+  if (n_steps == 0 || S->B == 0) return BODEX_OK;
+  RefineArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.hand = h->dev;
+  A.tips = h->tips;
+  A.obj = o->dev;
+  A.B = S->B;
+  A.pc = p_coarse;
+  A.delta = delta;
+  A.w_d = p->energy.w_d;
+  A.w_qp = w_qp;
+  A.lr_t = p->lr_t;
+  A.lr_r = p->lr_r;
+  A.b1 = p->b1;
+  A.b2 = p->b2;
+  A.adam_eps = p->adam_eps;
+  A.n_steps = n_steps;
+  A.t0 = S->t;
+  A.x = S->x;
+  A.am = S->am;
+  A.av = S->av;
+  A.E = E_last;
+  A.kstar = kstar;
+  A.status = status;
+  int r;
+  switch (h->host.m) {
+    case 3: r = run_refine<3>(A, as_stream(stream)); break;
+    case 4: r = run_refine<4>(A, as_stream(stream)); break;
+    case 5: r = run_refine<5>(A, as_stream(stream)); break;
+    default: return fail(BODEX_ERR_INVALID, "unsupported m");
+  }
   if (r == BODEX_OK) S->t += n_steps;
   return r;
 }

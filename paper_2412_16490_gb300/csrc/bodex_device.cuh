@@ -133,12 +133,11 @@ __device__ __forceinline__ void root_frame(const float* x, Tf& T, float om[3][3]
   om[2][0] = s2;  om[2][1] = -s1 * c2; om[2][2] = c1 * c2;
 }
 
-// Forward kinematics for contact i (Sec. IV-B): walks the chain from the
-// root to the contact link.  Returns c_{i,w}; if `jw` is given, stores the
-// world axis and a point on the axis of every chain joint (6 floats each,
-// in chain order) for the adjoint.
-__device__ inline void fk_contact(const HandDev& H, int i, const float* x, float* c, float* jw) {
-  Tf T;
+// Forward kinematics of contact i's link (Sec. IV-B): walks the chain from
+// the root and returns the link frame T; if `jw` is given, stores the world
+// axis and a point on the axis of every chain joint (6 floats each, in chain
+// order) for the adjoint.
+__device__ inline void fk_link(const HandDev& H, int i, const float* x, Tf& T, float* jw) {
   float om[3][3];
   root_frame(x, T, om);
   const int L = H.chain_len[i];
@@ -165,6 +164,18 @@ __device__ inline void fk_contact(const HandDev& H, int i, const float* x, float
     rq.t[0] = rq.t[1] = rq.t[2] = 0.f;
     tf_mul(base, rq, T);
   }
+}
+
+__device__ __forceinline__ void tf_point(const Tf& T, const float* p, float* c) {
+  c[0] = fmaf(T.R[0], p[0], fmaf(T.R[1], p[1], fmaf(T.R[2], p[2], T.t[0])));
+  c[1] = fmaf(T.R[3], p[0], fmaf(T.R[4], p[1], fmaf(T.R[5], p[2], T.t[1])));
+  c[2] = fmaf(T.R[6], p[0], fmaf(T.R[7], p[1], fmaf(T.R[8], p[2], T.t[2])));
+}
+
+// Contact point c_{i,w} = R c_{i,l} + T of contact i (and chain frames, see fk_link).
+__device__ inline void fk_contact(const HandDev& H, int i, const float* x, float* c, float* jw) {
+  Tf T;
+  fk_link(H, i, x, T, jw);
   const float* cl = H.clocal[i];
   c[0] = fmaf(T.R[0], cl[0], fmaf(T.R[1], cl[1], fmaf(T.R[2], cl[2], T.t[0])));
   c[1] = fmaf(T.R[3], cl[0], fmaf(T.R[4], cl[1], fmaf(T.R[5], cl[2], T.t[1])));

@@ -295,3 +295,17 @@ def test_run_decreases_energy_tiny():
     E1 = O.evaluate(H, Ob, x, T, P)["E"]
     assert (E1 < E0).all()
     assert (x >= hand.qmin - 1e-12).all() and (x <= hand.qmax + 1e-12).all()
+
+
+@pytest.mark.parametrize("wl", ["tiny", "grad"])
+def test_regularised_energy_gradient_is_exact(wl):
+    """With eps |y|^2 the optimum is unique and Q is the regularised optimal
+    value, so the envelope-theorem chain is the exact derivative of E: every
+    instance agrees with central differences."""
+    hand, obj, x0, T, P, _, _ = I.workload(wl, batch=16)
+    P = dict(P, eps_reg=1e-3)
+    H, Ob = O.Hand(hand), O.Object(obj)
+    ev = O.evaluate(H, Ob, x0, T, P)
+    gfd = O.grad_fd(H, Ob, x0, T, P, step=1e-6)
+    rel = np.linalg.norm(ev["grad"] - gfd, axis=1) / np.linalg.norm(gfd, axis=1)
+    assert (rel < 1e-7).all(), rel

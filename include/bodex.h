@@ -63,6 +63,7 @@ extern "C" {
 #define BODEX_MAX_JOINTS 32   /* revolute joints per hand */
 #define BODEX_MAX_CONTACTS 5  /* m in {3, 4, 5} are compiled */
 #define BODEX_MAX_CHAIN 8     /* joints between the root and a contact link */
+#define BODEX_MAX_JOBS 64     /* jobs per bodex_step_multi launch */
 
 typedef struct bodex_hand_s* bodex_hand_t;
 typedef struct bodex_object_s* bodex_object_t;
@@ -165,6 +166,8 @@ typedef struct bodex_step_params {
   float lr_t, lr_r, b1, b2, adam_eps;
   bodex_energy_params energy;
   bodex_qp_params qp;
+  int grasps_per_cta;  /* CTA tile: grasps per thread block (0 = default, 96 / s); an
+                          autotuner knob that changes speed, never results */
 } bodex_step_params;
 
 /* ---------------------------------------------------------------- calls */
@@ -210,6 +213,10 @@ int bodex_state_destroy(bodex_state_t state);
 int bodex_state_set_pose(bodex_state_t state, const float* x, void* stream);
 /* Copies the pose to a device array [B,D]. */
 int bodex_state_get_pose(bodex_state_t state, float* x, void* stream);
+/* Copies, for each grasp, the largest ADMM residual (max of the primal and
+ * dual inf-norms over its s QPs) at the last upper iteration of the last
+ * bodex_step / bodex_step_multi launch into res [B] (device). */
+int bodex_state_get_residual(bodex_state_t state, float* res, void* stream);
 /* Copies the Adam moments m, v [B,D] (either may be NULL) and returns the step count. */
 int bodex_state_get_adam(bodex_state_t state, float* m, float* v, int* step, void* stream);
 
@@ -226,6 +233,28 @@ int bodex_state_get_adam(bodex_state_t state, float* m, float* v, int* step, voi
 int bodex_energy_grad(bodex_hand_t hand, bodex_object_t obj, const float* x, int B, const float* T, int s,
                       const bodex_step_params* params, bodex_state_t warm, float* E, float* dEdx, float* Q,
                       float* y, int32_t* status, void* stream);
+
+/* One launch of fused upper iterations for several jobs at once: jobs may
+ * use different hand templates (m = 3, 4, 5), objects, batch sizes, wrench
+ * sets and step counts.  Each CTA runs one job's tile of grasps; a grasp's
+ * result is the same as with bodex_step on its own state (the per-grasp
+ * arithmetic does not depend on the other jobs).  The job table travels in
+ * the kernel parameters: the call allocates no device memory.  Jobs with
+ * B = 0 or n_steps = 0 are skipped; each state's step counter advances by
+ * its job's n_steps.
+ * Errors: BODEX_ERR_INVALID (n_jobs outside 0..BODEX_MAX_JOBS, null handle,
+ * shape mismatch), BODEX_ERR_INFEASIBLE, BODEX_ERR_CUDA. */
+typedef struct bodex_job {
+  bodex_hand_t hand;
+  bodex_object_t obj;
+  bodex_state_t state;  /* created for this hand and s */
+  const float* T;       /* [s,6] device */
+  int s;
+  int n_steps;          /* upper iterations for this job in this launch */
+  float* E_last;        /* [B] or NULL */
+  int32_t* status;      /* [B] or NULL */
+} bodex_job;
+int bodex_step_multi(const bodex_job* jobs, int n_jobs, const bodex_step_params* params, void* stream);
 
 /* Backward pass of the energy for forces y from an earlier solve (the
  * hand-written adjoint behind the autograd binding): recomputes FK, the SDF

@@ -19,7 +19,7 @@ from ._binding import BodexError, ST_DEGENERATE_NORMAL, ST_NONFINITE, ST_NOT_CON
 __all__ = [
     "load", "Hand", "Object", "State", "qp_params", "step_params",
     "bodex_hand_create", "bodex_object_create", "bodex_state_create",
-    "bodex_fk_contacts", "bodex_qp_solve_batch", "bodex_energy_grad", "bodex_energy_adjoint", "bodex_step", "bodex_refine",
+    "bodex_fk_contacts", "bodex_qp_solve_batch", "bodex_energy_grad", "bodex_energy_adjoint", "bodex_step", "bodex_step_multi", "bodex_refine",
     "synthesize",
     "bodex_sync", "bodex_version", "BodexError",
 ]
@@ -63,7 +63,8 @@ def qp_params(mu=0.5, beta=1.0, gamma=0.5, rho=0.1, sigma=1e-6, alpha=1.6, eps_a
                               int(check_every), int(warm), int(strict))
 
 
-def step_params(params: dict | None = None, qp: _b.bodex_qp_params | None = None) -> _b.bodex_step_params:
+def step_params(params: dict | None = None, qp: _b.bodex_qp_params | None = None,
+                grasps_per_cta: int = 0) -> _b.bodex_step_params:
     """Upper-level parameters (struct bodex_step_params) from a dict with keys
     lr_t, lr_r, b1, b2, adam_eps, w_q, w_d, delta (and mu, beta, gamma, eps_reg
     used when `qp` is not given)."""
@@ -74,7 +75,7 @@ def step_params(params: dict | None = None, qp: _b.bodex_qp_params | None = None
     if qp is None:
         qp = qp_params(mu=p["mu"], beta=p["beta"], gamma=p["gamma"], eps_reg=p["eps_reg"])
     return _b.bodex_step_params(p["lr_t"], p["lr_r"], p["b1"], p["b2"], p["adam_eps"],
-                                _b.bodex_energy_params(p["w_q"], p["w_d"], p["delta"]), qp)
+                                _b.bodex_energy_params(p["w_q"], p["w_d"], p["delta"]), qp, int(grasps_per_cta))
 
 
 # ---------------------------------------------------------------- handles
@@ -168,6 +169,13 @@ class State:
         x = torch.empty((self.B, self.D), dtype=torch.float32, device="cuda")
         _b.check(load().bodex_state_get_pose(self._s, _ptr(x), _stream(stream)))
         return x
+
+    def residual(self, stream=None):
+        """Per-grasp max ADMM residual at the last step of the last launch [B]."""
+        torch = _torch()
+        r = torch.empty(self.B, dtype=torch.float32, device="cuda")
+        _b.check(load().bodex_state_get_residual(self._s, _ptr(r), _stream(stream)))
+        return r
 
     def adam(self, stream=None):
         torch = _torch()
@@ -297,6 +305,18 @@ def synthesize(hand: Hand, obj: Object, x0, T, params: _b.bodex_step_params, coa
     bodex_refine(hand, obj, st, pc, final_steps, 0.0, w_qp, params, E_last=E, stream=stream)
     x = st.pose(stream)
     return dict(x_p=xp, x=x, x_s=2.0 * x - xp, E=E)
+
+
+def bodex_step_multi(jobs, params: _b.bodex_step_params, stream=None):
+    """One launch for several jobs.  jobs: iterable of dicts with keys hand,
+    obj, state, T, n_steps and optionally E_last, status (CUDA tensors)."""
+    jobs = list(jobs)
+    arr = (_b.bodex_job * max(1, len(jobs)))()
+    for k, j in enumerate(jobs):
+        T = j["T"]
+        arr[k] = _b.bodex_job(j["hand"].handle, j["obj"].handle, j["state"].handle, _ptr(T), int(T.shape[0]),
+                              int(j["n_steps"]), _ptr(j.get("E_last")), _ptr(j.get("status")))
+    _b.check(load().bodex_step_multi(arr, len(jobs), C.byref(params), _stream(stream)))
 
 
 def bodex_sync(stream=None):

@@ -30,6 +30,7 @@ EXPORTS = (
     "bodex_hand_create", "bodex_hand_destroy", "bodex_object_create", "bodex_object_destroy",
     "bodex_object_gravity_centre", "bodex_fk_contacts", "bodex_qp_solve_batch", "bodex_state_create",
     "bodex_state_destroy", "bodex_state_set_pose", "bodex_state_get_pose", "bodex_state_get_adam",
+    "bodex_state_get_residual", "bodex_step_multi",
     "bodex_energy_grad", "bodex_energy_adjoint", "bodex_step", "bodex_refine", "bodex_step_noalloc", "bodex_sync", "bodex_last_error", "bodex_version",
 )
 
@@ -58,7 +59,16 @@ class bodex_energy_params(C.Structure):
 
 class bodex_step_params(C.Structure):
     _fields_ = [("lr_t", C.c_float), ("lr_r", C.c_float), ("b1", C.c_float), ("b2", C.c_float),
-                ("adam_eps", C.c_float), ("energy", bodex_energy_params), ("qp", bodex_qp_params)]
+                ("adam_eps", C.c_float), ("energy", bodex_energy_params), ("qp", bodex_qp_params),
+                ("grasps_per_cta", C.c_int)]
+
+
+class bodex_job(C.Structure):
+    _fields_ = [("hand", C.c_void_p), ("obj", C.c_void_p), ("state", C.c_void_p), ("T", C.c_void_p),
+                ("s", C.c_int), ("n_steps", C.c_int), ("E_last", C.c_void_p), ("status", C.c_void_p)]
+
+
+BODEX_MAX_JOBS = 64
 
 
 _lib = None
@@ -103,6 +113,8 @@ def load(build_if_missing: bool = True):
         "bodex_state_set_pose": [v, v, v],
         "bodex_state_get_pose": [v, v, v],
         "bodex_state_get_adam": [v, v, v, C.POINTER(C.c_int), v],
+        "bodex_state_get_residual": [v, v, v],
+        "bodex_step_multi": [C.POINTER(bodex_job), C.c_int, C.POINTER(bodex_step_params), v],
         "bodex_energy_grad": [v, v, v, C.c_int, v, C.c_int, C.POINTER(bodex_step_params), v, v, v, v, v, v, v],
         "bodex_energy_adjoint": [v, v, v, C.c_int, v, C.c_int, C.POINTER(bodex_step_params), v, v, v, v, v],
         "bodex_step": [v, v, v, v, C.c_int, C.c_int, C.POINTER(bodex_step_params), v, v, v],

@@ -61,6 +61,7 @@ struct bodex_state_s {
   float* av = nullptr;
   float* qy = nullptr;  // [B, s, 3m]
   float* qw = nullptr;  // [B, s, 9m+1]
+  float* res = nullptr;  // [B] max QP residual at the last step of the last launch
   int t = 0;
 };
 
@@ -178,12 +179,13 @@ __global__ void __launch_bounds__(128) fk_contacts_kernel(const HandDev* __restr
 // ============================================================================ per-grasp QP setup (shared by kernels)
 // K^-1 of every grasp of the CTA (Woodbury form, all lanes); must be called
 // by every thread of the CTA (contains barriers).
-// Double precision when the solve iterates to a residual target, single
-// precision for fixed-iteration solves (the branch is uniform per launch).
+// Double precision when the host asks for it (solves that iterate to a
+// tight residual target), single precision otherwise; the branch is
+// uniform per launch.
 template <int M>
 __device__ inline void setup_kinv(bool active, int lane, int S, const float* Gs, float* scratch, float* Kinv,
                                   const AdmmCfg& cfg) {
-  if (cfg.eps > 0.f) setup_kinv_woodbury<M, double>(active, lane, S, Gs, scratch, Kinv, cfg);
+  if (cfg.fp64_setup) setup_kinv_woodbury<M, double>(active, lane, S, Gs, scratch, Kinv, cfg);
   else setup_kinv_woodbury<M, float>(active, lane, S, Gs, scratch, Kinv, cfg);
 }
 
@@ -288,6 +290,8 @@ struct FusedArgs {
   float* yout;
   int32_t* status;
   const float* yin;  // MODE_ADJOINT: forces from a previous solve [B, s, 3m]
+  float* res;        // [B] max ADMM residual of the grasp's QPs at the last step (may be null)
+  int gpb;           // grasps per CTA
 };
 
 // MODE_EVAL: E and dE/dx at x.  MODE_STEP: n_steps upper iterations on the
@@ -295,16 +299,16 @@ struct FusedArgs {
 // the backward pass of the energy, with FK and the SDF query recomputed.
 enum { MODE_EVAL = 0, MODE_STEP = 1, MODE_ADJOINT = 2 };
 
+// The work of one CTA: GPB grasps (cta * GPB ...) of one job, s lanes each;
+// threads beyond GPB * s idle but take part in every barrier.
 template <int M, int MODE>
-__global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
+__device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, float* smem) {
   using L = Lay<M>;
   constexpr int NV = L::NV, NC = L::NC;
-  extern __shared__ __align__(16) float smem[];
   copy_hand_to_smem(A.hand, smem);
   const int S = A.S;
-  const int GPB = blockDim.x / S;
   const int gl = threadIdx.x / S, lane = threadIdx.x % S;
-  const int b = blockIdx.x * GPB + gl;
+  const int b = cta * GPB + gl;
   const bool active = (gl < GPB) && (b < A.B);
   const HandDev& H = *reinterpret_cast<const HandDev*>(smem);
   float* kin = smem + L::HAND_WORDS + gl * L::KS;
@@ -328,7 +332,10 @@ __global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
         avs[k] = A.av[(size_t)b * D + k];
       }
     }
-    if (lane == 0) *stat = 0;
+    if (lane == 0) {
+      *stat = 0;
+      sc[2] = 0.f;  // max residual of the grasp's QPs at the last step
+    }
   }
   // ADMM warm start of this lane's QP, kept in registers across steps
   float y[NV], w[NC];
@@ -378,6 +385,7 @@ __global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
         neg_q<M>(Gs, t, cfg.beta, mq);
         float rp, rd;
         admm_solve<M>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
+        if (step == A.n_steps - 1) atomicMax(reinterpret_cast<int*>(sc + 2), __float_as_int(fmaxf(rp, rd)));
       }
       float* ry = per + L::oRY + lane * (6 + NV);
       float Q = 0.f;
@@ -494,6 +502,7 @@ __global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
   if (lane == 0) {
     if (A.E) A.E[b] = sc[0];
     if (A.status) A.status[b] = *stat;
+    if (A.res) A.res[b] = sc[2];
   }
   if (MODE == MODE_STEP) {
     for (int k = lane; k < D; k += S) {
@@ -513,6 +522,41 @@ __global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
     if (A.yout)
 #pragma unroll
       for (int a = 0; a < NV; ++a) A.yout[q * NV + a] = y[a];
+  }
+}
+
+template <int M, int MODE>
+__global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  fused_cta<M, MODE>(A, blockIdx.x, A.gpb, smem);
+}
+
+// ============================================================================ kernel: several jobs in one launch
+// Jobs with different hand templates (m = 3, 4, 5), objects, batch sizes,
+// wrench sets and step counts share one launch: CTA c belongs to the job j
+// with cta_begin[j] <= c < cta_begin[j+1] and runs that job's fused step on
+// its tile of grasps.  The table travels in the kernel parameters, so a
+// launch needs no device memory of its own.
+struct MultiArgs {
+  int n_jobs;
+  int m[BODEX_MAX_JOBS];
+  int cta_begin[BODEX_MAX_JOBS + 1];
+  FusedArgs job[BODEX_MAX_JOBS];
+};
+
+static_assert(sizeof(MultiArgs) <= 32000, "job table must fit in the kernel parameter space");
+
+__global__ void __launch_bounds__(CTA_LANES, 4) multi_kernel(const __grid_constant__ MultiArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  const int c = blockIdx.x;
+  int j = 0;
+  while (j + 1 < A.n_jobs && c >= A.cta_begin[j + 1]) ++j;
+  const FusedArgs& J = A.job[j];
+  const int cta = c - A.cta_begin[j];
+  switch (A.m[j]) {
+    case 3: fused_cta<3, MODE_STEP>(J, cta, J.gpb, smem); break;
+    case 4: fused_cta<4, MODE_STEP>(J, cta, J.gpb, smem); break;
+    default: fused_cta<5, MODE_STEP>(J, cta, J.gpb, smem); break;
   }
 }
 
@@ -687,6 +731,14 @@ int gpb_for(int s) {
   return std::max(1, std::min(CTA_LANES / s, (int)fit));
 }
 
+// Grasps per CTA: the requested count (autotuner), else the default,
+// never more than fit in 96 lanes and in shared memory.
+template <int M>
+int pick_gpb(int s, int requested) {
+  const int cap = gpb_for<M>(s);
+  return requested > 0 ? std::min(requested, cap) : cap;
+}
+
 template <class K>
 int ensure_smem(K kernel, size_t bytes) {
   // A launch reports errors through cudaGetLastError; clear what an earlier,
@@ -720,8 +772,10 @@ int launch_err(const char* what) {
 }
 
 template <int M>
-int run_fused(int mode, const FusedArgs& A, cudaStream_t st) {
-  const int gpb = gpb_for<M>(A.S);
+int run_fused(int mode, const FusedArgs& A0, cudaStream_t st) {
+  FusedArgs A = A0;
+  A.gpb = pick_gpb<M>(A.S, A0.gpb);
+  const int gpb = A.gpb;
   const size_t bytes = Lay<M>::bytes(gpb);
   const dim3 grid((A.B + gpb - 1) / gpb), block(gpb * A.S);
   if (A.B == 0) return BODEX_OK;
@@ -981,7 +1035,8 @@ int bodex_qp_solve_batch(const float* G, int B, int m, const float* T, int s, co
   if (B > 0 && (!G || !T || !y || !z || !lam || !Q)) return fail(BODEX_ERR_INVALID, "null array");
   if (int r = check_qp_params(params, m)) return r;
   if (params->strict && !status) return fail(BODEX_ERR_INVALID, "strict mode needs a status array");
-  const AdmmCfg cfg = admm_cfg(*params);
+  AdmmCfg cfg = admm_cfg(*params);
+  cfg.fp64_setup = params->eps_abs > 0.f ? 1 : 0;  // one setup per call: exact inverse is cheap
   cudaStream_t st = as_stream(stream);
   int r;
   switch (m) {
@@ -1008,9 +1063,9 @@ int bodex_state_create(bodex_hand_t h, int B, int s, bodex_state_t* out) {
   S->m = h->host.m;
   S->D = h->host.D;
   const size_t nx = (size_t)B * S->D, ny = (size_t)B * s * 3 * S->m, nw = (size_t)B * s * (9 * S->m + 1);
-  float** bufs[5] = {&S->x, &S->am, &S->av, &S->qy, &S->qw};
-  const size_t cnt[5] = {nx, nx, nx, ny, nw};
-  for (int k = 0; k < 5; ++k) {
+  float** bufs[6] = {&S->x, &S->am, &S->av, &S->qy, &S->qw, &S->res};
+  const size_t cnt[6] = {nx, nx, nx, ny, nw, (size_t)B};
+  for (int k = 0; k < 6; ++k) {
     if (cnt[k] == 0) continue;
     if (cudaMalloc(bufs[k], cnt[k] * sizeof(float)) != cudaSuccess) {
       for (int j = 0; j < k; ++j) cudaFree(*bufs[j]);
@@ -1025,6 +1080,7 @@ int bodex_state_create(bodex_hand_t h, int B, int s, bodex_state_t* out) {
 
 int bodex_state_destroy(bodex_state_t S) {
   if (!S) return BODEX_OK;
+  cudaFree(S->res);
   cudaFree(S->x);
   cudaFree(S->am);
   cudaFree(S->av);
@@ -1052,6 +1108,14 @@ int bodex_state_get_pose(bodex_state_t S, float* x, void* stream) {
   if (!S || (!x && S->B > 0)) return fail(BODEX_ERR_INVALID, "null argument");
   if (S->B == 0) return BODEX_OK;
   BODEX_CUDA(cudaMemcpyAsync(x, S->x, (size_t)S->B * S->D * sizeof(float), cudaMemcpyDeviceToDevice,
+                             as_stream(stream)));
+  return BODEX_OK;
+}
+
+int bodex_state_get_residual(bodex_state_t S, float* res, void* stream) {
+  if (!S || (!res && S->B > 0)) return fail(BODEX_ERR_INVALID, "null argument");
+  if (S->B == 0) return BODEX_OK;
+  BODEX_CUDA(cudaMemcpyAsync(res, S->res, (size_t)S->B * sizeof(float), cudaMemcpyDeviceToDevice,
                              as_stream(stream)));
   return BODEX_OK;
 }
@@ -1084,6 +1148,10 @@ static int fill_args(FusedArgs& A, bodex_hand_t h, bodex_object_t o, const float
   A.b1 = p->b1;
   A.b2 = p->b2;
   A.adam_eps = p->adam_eps;
+  // a tight residual target moves ADMM's fixed point with the backward
+  // error of K^-1: build it in double there
+  A.cfg.fp64_setup = (p->qp.eps_abs > 0.f && p->qp.eps_abs <= 2e-6f) ? 1 : 0;
+  A.gpb = p->grasps_per_cta;
   return BODEX_OK;
 }
 
@@ -1139,8 +1207,76 @@ int bodex_step(bodex_hand_t h, bodex_object_t o, bodex_state_t S, const float* T
   A.qw = S->qw;
   A.E = E_last;
   A.status = status;
+  A.res = S->res;
   const int r = dispatch_fused(h->host.m, MODE_STEP, A, as_stream(stream));
   if (r == BODEX_OK) S->t += n_steps;
+  return r;
+}
+
+int bodex_step_multi(const bodex_job* jobs, int n_jobs, const bodex_step_params* params, void* stream) {
+  if (n_jobs < 0 || n_jobs > BODEX_MAX_JOBS || (n_jobs > 0 && !jobs) || !params)
+    return fail(BODEX_ERR_INVALID, "n_jobs must be 0..BODEX_MAX_JOBS with a job array");
+  MultiArgs* MA = new MultiArgs();  // ~15 KB: kept off the host stack
+  std::memset(MA, 0, sizeof(MultiArgs));
+  size_t bytes = 0;
+  int total = 0, nj = 0;
+  int take[BODEX_MAX_JOBS];
+  for (int j = 0; j < n_jobs; ++j) {
+    const bodex_job& J = jobs[j];
+    bodex_state_t S = J.state;
+    if (!J.hand || !J.obj || !S) {
+      delete MA;
+      return fail(BODEX_ERR_INVALID, "job with a null handle");
+    }
+    if (S->s != J.s || S->m != J.hand->host.m || S->D != J.hand->host.D || J.n_steps < 0) {
+      delete MA;
+      return fail(BODEX_ERR_INVALID, "job state shape mismatch or n_steps < 0");
+    }
+    if (S->B == 0 || J.n_steps == 0) continue;
+    FusedArgs& A = MA->job[nj];
+    if (int r = fill_args(A, J.hand, J.obj, J.T, J.s, S->B, params)) {
+      delete MA;
+      return r;
+    }
+    const int m = J.hand->host.m;
+    int gpb = 0;
+    size_t b = 0;
+    switch (m) {
+      case 3: gpb = pick_gpb<3>(J.s, A.gpb); b = Lay<3>::bytes(gpb); break;
+      case 4: gpb = pick_gpb<4>(J.s, A.gpb); b = Lay<4>::bytes(gpb); break;
+      default: gpb = pick_gpb<5>(J.s, A.gpb); b = Lay<5>::bytes(gpb); break;
+    }
+    A.gpb = gpb;
+    A.n_steps = J.n_steps;
+    A.t0 = S->t;
+    A.x_state = S->x;
+    A.am = S->am;
+    A.av = S->av;
+    A.qy = S->qy;
+    A.qw = S->qw;
+    A.E = J.E_last;
+    A.status = J.status;
+    A.res = S->res;
+    MA->m[nj] = m;
+    MA->cta_begin[nj] = total;
+    total += (S->B + gpb - 1) / gpb;
+    bytes = std::max(bytes, b);
+    take[nj] = j;
+    ++nj;
+  }
+  MA->n_jobs = nj;
+  MA->cta_begin[nj] = total;
+  int r = BODEX_OK;
+  if (nj > 0) {
+    r = ensure_smem(multi_kernel, bytes);
+    if (r == BODEX_OK) {
+      multi_kernel<<<total, CTA_LANES, bytes, as_stream(stream)>>>(*MA);
+      r = launch_err("multi_kernel launch");
+    }
+    if (r == BODEX_OK)
+      for (int k = 0; k < nj; ++k) jobs[take[k]].state->t += jobs[take[k]].n_steps;
+  }
+  delete MA;
   return r;
 }
 

@@ -54,6 +54,7 @@ struct AdmmCfg {
   float mu_c8;  // mu cos(pi/8)
   float beta, gamma, rho, sigma, alpha, eps, eps_reg;
   int iters, check;
+  int fp64_setup;  // build K^-1 in double (set by the host per launch)
 };
 
 __host__ __device__ inline AdmmCfg admm_cfg(const bodex_qp_params& p) {
@@ -68,6 +69,7 @@ __host__ __device__ inline AdmmCfg admm_cfg(const bodex_qp_params& p) {
   c.eps_reg = p.eps_reg;
   c.iters = p.max_iter;
   c.check = p.check_every > 0 ? p.check_every : 10;
+  c.fp64_setup = 0;
   return c;
 }
 

@@ -1,0 +1,78 @@
+"""Mixed-template persistent launch (bodex_step_multi): jobs with hand
+templates of m = 3, 4, 5 contacts, different objects, batch sizes and step
+counts in one launch give each job the result it gets alone."""
+import numpy as np
+import pytest
+
+from gpu_helpers import I, cuda, host, torch
+
+import paper_2412_16490_gb300 as bx
+
+pytestmark = pytest.mark.gpu
+
+
+def _jobs():
+    specs = [("hand3", I.grid_object(4, n=48), 37, 5), ("hand4x4", I.sphere_object(), 50, 7),
+             ("hand5", I.grid_object(2), 29, 3), ("hand4", I.grid_object(6, n=56), 11, 6)]
+    out = []
+    for k, (name, obj, B, n) in enumerate(specs):
+        hand = I.hand_template(name)
+        x0 = I.initial_poses(hand, obj, B, seed=30 + k)
+        out.append(dict(tpl=hand, objd=obj, x0=x0, B=B, n=n))
+    return out
+
+
+def test_multi_launch_matches_single_launches():
+    T = cuda(I.wrench_set(12))
+    sp = bx.step_params(I.default_params(), qp=bx.qp_params(max_iter=30))
+    jobs = _jobs()
+    for j in jobs:
+        j["hand"], j["obj"] = bx.Hand(j["tpl"]), bx.Object(j["objd"])
+        j["mix"], j["alone"] = bx.State(j["hand"], j["B"], 12), bx.State(j["hand"], j["B"], 12)
+        j["mix"].set_pose(cuda(j["x0"]))
+        j["alone"].set_pose(cuda(j["x0"]))
+    bx.bodex_step_multi([dict(hand=j["hand"], obj=j["obj"], state=j["mix"], T=T, n_steps=j["n"]) for j in jobs], sp)
+    for j in jobs:
+        bx.bodex_step(j["hand"], j["obj"], j["alone"], T, j["n"], sp)
+    torch.cuda.synchronize()
+    for j in jobs:
+        a, b = host(j["mix"].pose()), host(j["alone"].pose())
+        np.testing.assert_allclose(a, b, atol=1e-6, err_msg=j["tpl"].name)
+        assert j["mix"].adam()[2] == j["n"]
+
+
+def test_cta_tile_does_not_change_results():
+    hand, obj, x0, T, P, _, _ = I.workload("paper", batch=70)
+    H, Ob = bx.Hand(hand), bx.Object(obj)
+    poses = []
+    for g in (2, 4, 8, 0):
+        sp = bx.step_params(P, qp=bx.qp_params(max_iter=20), grasps_per_cta=g)
+        st = bx.State(H, 70, 12)
+        st.set_pose(cuda(x0))
+        bx.bodex_step(H, Ob, st, cuda(T), 4, sp)
+        poses.append(st.pose())
+    for p in poses[1:]:
+        assert torch.equal(p, poses[0])
+
+
+def test_residual_output_tracks_admm_iterations():
+    hand, obj, x0, T, P, _, _ = I.workload("tiny", batch=40)
+    H, Ob = bx.Hand(hand), bx.Object(obj)
+    res = []
+    for iters in (5, 200):
+        st = bx.State(H, 40, 6)
+        st.set_pose(cuda(x0))
+        bx.bodex_step(H, Ob, st, cuda(T), 3, bx.step_params(P, qp=bx.qp_params(max_iter=iters)))
+        res.append(host(st.residual()))
+    assert np.isfinite(res[0]).all() and (res[0] > 0).all()
+    assert np.median(res[1]) < 0.2 * np.median(res[0])
+
+
+def test_multi_launch_rejects_bad_tables():
+    hand = I.hand_template("hand4")
+    H, Ob = bx.Hand(hand), bx.Object(I.sphere_object())
+    st = bx.State(H, 4, 6)
+    T = cuda(I.wrench_set(12))  # s = 12 does not match the state's s = 6
+    with pytest.raises(bx.BodexError):
+        bx.bodex_step_multi([dict(hand=H, obj=Ob, state=st, T=T, n_steps=1)], bx.step_params())
+    bx.bodex_step_multi([], bx.step_params())  # empty table is a no-op

@@ -255,6 +255,9 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.quick:
         extra["qp_solves"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev)
         extra["e2e"] = e2e_rate(bx, torch, H, Ob, st, x0, T_dev, sp)
+        extra["persistent_mixed"] = persistent_mixed(bx, torch, P)
+        if args.serve_jobs > 0:
+            extra["serving"] = serving_latency(bx, torch, P, args.serve_jobs)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         (cpu_rate, cpu_dt, cores), g = calibrated_oracle_sample(args.cpu_seconds, seed=2)
         extra["cpu_baseline"] = {"value": cpu_rate, "unit": "grasps/s", "cores": cores, "kind": "oracle",
@@ -282,7 +285,131 @@ def run_ours(args, rank, world, local_rank):
     if "e2e" in extra:
         line["e2e"] = extra.pop("e2e")
     line.update(extra)
+    if "serving" in line:
+        cb = line["serving"]["continuous_batching"]
+        line["p50_job_latency_s"], line["p99_job_latency_s"] = cb["p50_s"], cb["p99_s"]
+    if "qp_solves" in line:
+        line["qp_solves_per_s"] = line["qp_solves"]["value"]
     print(json.dumps(line), flush=True)
+
+
+def _timed(torch, fn, reps=3):
+    out = []
+    for r in range(reps + 1):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        if r:
+            out.append(a.elapsed_time(b))
+    return float(np.median(out))
+
+
+def persistent_mixed(bx, torch, P):
+    """Mixed-template batch (3-finger/3-contact, 4-finger/4-contact,
+    5-finger/5-contact hands; 512 / 2048 / 6144 grasps over six grids of
+    48-96 nodes), 200 upper steps x 50 ADMM iterations, four ways:
+    one persistent launch for all jobs; one launch per job and upper step;
+    that per-step loop captured once in a CUDA graph and replayed; and the
+    persistent launch with the autotuner's CTA tile and ADMM schedule."""
+    from paper_2412_16490_gb300.autotune import autotune, tuned_params
+    jobs, T = I.mixed_workload(seed=4)
+    Tt = torch.as_tensor(T).cuda()
+    sp = bx.step_params(P, qp=bx.qp_params(max_iter=ADMM_ITERS))
+    hands = {}
+    J = []
+    for hand, obj, x0 in jobs:
+        if hand.name not in hands:
+            hands[hand.name] = bx.Hand(hand)
+        H = hands[hand.name]
+        J.append(dict(hand=H, obj=bx.Object(obj), state=bx.State(H, x0.shape[0], 12), T=Tt,
+                      x0=torch.as_tensor(x0).cuda(), tpl=hand))
+    grasps = sum(int(j["x0"].shape[0]) for j in J)
+
+    def reset():
+        for j in J:
+            j["state"].set_pose(j["x0"])
+
+    def persistent(params):
+        reset()
+        bx.bodex_step_multi([dict(j, n_steps=N_STEPS) for j in J], params)
+
+    def per_step():
+        for _ in range(N_STEPS):
+            for j in J:
+                bx.bodex_step(j["hand"], j["obj"], j["state"], Tt, 1, sp)
+
+    def plain():
+        reset()
+        per_step()
+
+    ms_persistent = _timed(torch, lambda: persistent(sp))
+    ms_plain = _timed(torch, plain, reps=2)
+    reset()
+    per_step()  # warm-up outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    reset()
+    with torch.cuda.graph(g):
+        per_step()
+
+    def graph():
+        reset()
+        g.replay()
+
+    ms_graph = _timed(torch, graph)
+    big = max(J, key=lambda j: j["x0"].shape[0])
+    t0 = time.perf_counter()
+    tuned = autotune(big["hand"], big["obj"], big["x0"][:2048].contiguous(), Tt, P, steps=N_STEPS)
+    tune_s = time.perf_counter() - t0
+    ms_tuned = _timed(torch, lambda: persistent(tuned_params(tuned, P)))
+    res = torch.cat([j["state"].residual() for j in J])
+    return {"grasps": grasps, "jobs": len(J), "upper_steps": N_STEPS,
+            "persistent": {"ms": ms_persistent, "grasps_per_s": grasps / ms_persistent * 1e3, "launches": 1},
+            "per_step_launches": {"ms": ms_plain, "grasps_per_s": grasps / ms_plain * 1e3,
+                                  "launches": N_STEPS * len(J)},
+            "per_step_cuda_graph": {"ms": ms_graph, "grasps_per_s": grasps / ms_graph * 1e3,
+                                    "launches": N_STEPS * len(J)},
+            "autotuned_persistent": {"ms": ms_tuned, "grasps_per_s": grasps / ms_tuned * 1e3,
+                                     "grasps_per_cta": tuned["grasps_per_cta"], "schedule": tuned["schedule"],
+                                     "sample_median_E": tuned["median_E"],
+                                     "sample_reference_median_E": tuned["reference_median_E"],
+                                     "frac_res_le_1e-5": float((res <= 1e-5).float().mean().item()),
+                                     "tune_s": tune_s}}
+
+
+def serving_latency(bx, torch, P, n_jobs):
+    """Poisson arrivals (20 jobs/s, seeded) of jobs with 32-128^3 grids, one of
+    the three hand templates and 256-4096 grasps x 200 steps, served by the
+    continuous-batching server and by one-job-at-a-time per-step launches."""
+    from paper_2412_16490_gb300.serving import PlainServer, PoissonWorkload, Server, latency_stats
+    t0 = time.perf_counter()
+    specs = PoissonWorkload(n_jobs=n_jobs, rate=20.0, seed=5).build()
+    build_s = time.perf_counter() - t0
+    qp = bx.qp_params(max_iter=ADMM_ITERS)
+    warm = PoissonWorkload(n_jobs=3, rate=1000.0, seed=6, grid_choices=(32,), grasp_choices=(256,), n_steps=20).build()
+    Server(P, qp=qp).replay(warm, realtime=False)  # load the kernels
+    srv = Server(P, qp=qp, steps_per_tick=10)
+    cont = latency_stats(srv.replay(specs, realtime=True))
+    cont.update(launches=srv.launches, peak_active_jobs=srv.peak_active, steps_per_tick=10)
+    pl = PlainServer(P, qp=qp)
+    plain = latency_stats(pl.replay(specs, realtime=True))
+    plain.update(launches=pl.launches)
+    # saturated load: the first 60 jobs all submitted at once
+    burst = specs[:60]
+    for sp in burst:
+        sp.arrival = 0.0
+    bs = Server(P, qp=qp, steps_per_tick=10)
+    b_cont = latency_stats(bs.replay(burst, realtime=False))
+    b_cont.update(launches=bs.launches, peak_active_jobs=bs.peak_active)
+    bp = PlainServer(P, qp=qp)
+    b_plain = latency_stats(bp.replay(burst, realtime=False))
+    b_plain.update(launches=bp.launches)
+    return {"arrival_rate_per_s": 20.0, "jobs": n_jobs, "continuous_batching": cont, "plain_per_job": plain,
+            "burst_60_jobs": {"continuous_batching": b_cont, "plain_per_job": b_plain},
+            "workload_build_s": build_s}
 
 
 def qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev):
@@ -336,12 +463,13 @@ def e2e_rate(bx, torch, H, Ob, st, x0, T_dev, sp, reps=3):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--quick", action="store_true", help="skip the QP and e2e side measurements")
+    ap.add_argument("--serve-jobs", type=int, default=300, help="jobs in the serving measurement (0 skips it)")
     ap.add_argument("--upper-steps", type=int, default=N_STEPS,
                     help="upper iterations per run (200 for the bench line; fewer for profiler captures)")
     args = ap.parse_args()

@@ -33,7 +33,7 @@ import numpy as np
 __all__ = [
     "HandTemplate", "SphereObject", "GridObject", "hand_template",
     "sphere_object", "grid_object", "initial_poses", "wrench_set",
-    "default_params", "random_contacts", "HAND_NAMES", "workload",
+    "default_params", "random_contacts", "HAND_NAMES", "workload", "mixed_workload",
 ]
 
 DEG = math.pi / 180.0
@@ -419,3 +419,22 @@ def workload(name: str, batch: int | None = None):
         B = batch
     x0 = initial_poses(hand, obj, B, seed)
     return hand, obj, x0, wrench_set(s), default_params(), steps, iters
+
+
+def mixed_workload(seed: int = 4, scale: float = 1.0):
+    """The mixed-template batch: 3 hand templates (3-finger 9-joint with 3
+    contacts, 4-finger 16-joint with 4, 5-finger 22-joint with 5) with
+    uneven counts 512 / 2048 / 6144, each split over two objects, six grids
+    of 48, 56, 64, 72, 80 and 96 nodes per axis (2 mm).  Returns a list of
+    (hand, object, x0) and the wrench set (s = 12).  `scale` shrinks the
+    counts for tests."""
+    rng_seeds = [seed * 100 + k for k in range(6)]
+    grids = [grid_object(sd, n=n) for sd, n in zip(rng_seeds, (48, 56, 64, 72, 80, 96))]
+    jobs = []
+    for k, (name, count) in enumerate((("hand3", 512), ("hand4x4", 2048), ("hand5", 6144))):
+        hand = hand_template(name)
+        for half in range(2):
+            obj = grids[2 * k + half]
+            B = max(1, int(count * scale) // 2)
+            jobs.append((hand, obj, initial_poses(hand, obj, B, seed=seed * 1000 + 2 * k + half)))
+    return jobs, wrench_set(12)

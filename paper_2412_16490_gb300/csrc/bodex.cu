@@ -13,9 +13,11 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -739,19 +741,30 @@ int pick_gpb(int s, int requested) {
   return requested > 0 ? std::min(requested, cap) : cap;
 }
 
+// Raises the kernel's dynamic shared-memory limit when needed, once per
+// device and size (so that launches recorded into a CUDA graph issue no
+// attribute calls after the first).
 template <class K>
 int ensure_smem(K kernel, size_t bytes) {
   // A launch reports errors through cudaGetLastError; clear what an earlier,
   // already reported failure may have left behind (sticky device faults are
   // returned again by the next call regardless).
   (void)cudaGetLastError();
-  if (bytes > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) {
-      (void)cudaGetLastError();
-      return cuda_fail(e, "cudaFuncSetAttribute");
-    }
+  if (bytes <= 48 * 1024) return BODEX_OK;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> configured;  // (kernel, device) -> bytes
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = configured.find(key);
+  if (it != configured.end() && it->second >= bytes) return BODEX_OK;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return cuda_fail(e, "cudaFuncSetAttribute");
   }
+  configured[key] = bytes;
   return BODEX_OK;
 }
 

@@ -91,7 +91,9 @@ struct Lay {
   static constexpr int oAV = oAM + MAXD;
   static constexpr int oJW = oAV + MAXD;  // chain joint axes/points, M x MAXCHAIN x 6
   static constexpr int oSC = oJW + M * MAXCHAIN * 6;
-  static constexpr int PER = align4(oSC + 4);
+  // per-grasp stride == 12 (mod 32) words: the two or three grasps that
+  // share a warp then map the same offset to different banks
+  static constexpr int PER = align4(oSC + 4) + ((12 - align4(oSC + 4) % 32) + 32) % 32;
   static constexpr int HAND_WORDS = align4((int)(sizeof(HandDev) / 4));
   static size_t bytes(int gpb) { return 4u * (size_t)(HAND_WORDS + gpb * (KS + PER)); }
 };

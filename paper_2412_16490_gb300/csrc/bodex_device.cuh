@@ -12,6 +12,10 @@
 
 #include "../../include/bodex.h"
 
+#ifndef BODEX_ADMM_UNROLL2
+#define BODEX_ADMM_UNROLL2 0
+#endif
+
 namespace bodex {
 
 constexpr int MAXJ = BODEX_MAX_JOINTS;
@@ -541,6 +545,15 @@ template <int M>
 __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* mq, const float* Kinv,
                                                const AdmmCfg& c) {
   constexpr int NV = Admm<M>::NV, NVP = Admm<M>::NVP;
+  constexpr int Q4 = NVP / 4;
+  // K^-1 rows are read from shared memory in 16-byte loads; rows 0 and 1
+  // are requested before the rhs is formed, and row a+2 while row a is
+  // used, so that the load latency overlaps arithmetic.
+  float4 k0[Q4], k1[Q4], k2[Q4];
+#pragma unroll
+  for (int q = 0; q < Q4; ++q) k0[q] = lds128(Kinv + 4 * q);
+#pragma unroll
+  for (int q = 0; q < Q4; ++q) k1[q] = lds128(Kinv + NVP + 4 * q);
   // rhs = sigma y - q + rho A^T (2 Pi(w) - w), one contact at a time
   float rhs[NV];
   const float vsum = 2.f * fmaxf(w[9 * M], c.gamma) - w[9 * M];
@@ -556,23 +569,18 @@ __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* 
     rhs[3 * i + 1] = fmaf(c.sigma, y[3 * i + 1], fmaf(c.rho, gd, mq[3 * i + 1]));
     rhs[3 * i + 2] = fmaf(c.sigma, y[3 * i + 2], fmaf(c.rho, ge, mq[3 * i + 2]));
   }
-  // yt = K^-1 rhs: rows of K^-1 from shared memory in 16-byte loads, the
-  // loads of row a+1 issued before the FMAs of row a
+  // yt = K^-1 rhs
   float yt[NV];
-  constexpr int Q4 = NVP / 4;
-  float4 cur[Q4], nxt[Q4];
-#pragma unroll
-  for (int q = 0; q < Q4; ++q) cur[q] = lds128(Kinv + 4 * q);
 #pragma unroll
   for (int a = 0; a < NV; ++a) {
-    if (a + 1 < NV) {
+    if (a + 2 < NV) {
 #pragma unroll
-      for (int q = 0; q < Q4; ++q) nxt[q] = lds128(Kinv + (a + 1) * NVP + 4 * q);
+      for (int q = 0; q < Q4; ++q) k2[q] = lds128(Kinv + (a + 2) * NVP + 4 * q);
     }
     float s0 = 0.f, s1 = 0.f;
 #pragma unroll
     for (int q = 0; q < Q4; ++q) {
-      const float4 k4 = cur[q];
+      const float4 k4 = k0[q];
       const int b = 4 * q;
       if (b + 0 < NV) s0 = fmaf(k4.x, rhs[b + 0], s0);
       if (b + 1 < NV) s1 = fmaf(k4.y, rhs[b + 1], s1);
@@ -581,7 +589,10 @@ __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* 
     }
     yt[a] = s0 + s1;
 #pragma unroll
-    for (int q = 0; q < Q4; ++q) cur[q] = nxt[q];
+    for (int q = 0; q < Q4; ++q) {
+      k0[q] = k1[q];
+      k1[q] = k2[q];
+    }
   }
   // w <- w + alpha (A yt - Pi(w)),  y <- alpha yt + (1 - alpha) y
   const float al = c.alpha, bl = 1.0f - c.alpha;
@@ -697,8 +708,20 @@ __device__ inline int admm_solve(float* y, float* w, const float* mq, const floa
       }
     }
   } else {
+#if BODEX_ADMM_UNROLL2
+#pragma unroll 1
+    for (; it + 1 < c.iters; it += 2) {
+      admm_iteration<M>(y, w, mq, Kinv, c);
+      admm_iteration<M>(y, w, mq, Kinv, c);
+    }
+    if (it < c.iters) {
+      admm_iteration<M>(y, w, mq, Kinv, c);
+      ++it;
+    }
+#else
 #pragma unroll 1
     for (; it < c.iters; ++it) admm_iteration<M>(y, w, mq, Kinv, c);
+#endif
     admm_residuals<M>(y, w, mq, G, c, rp, rd);
   }
   return it;

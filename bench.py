@@ -34,6 +34,11 @@ WORKLOAD = "paper-scale: 4096 grasps, 5-finger 22-joint hand, 5 contacts, 64^3 S
            "12 wrenches, 200 upper steps x 50 ADMM iterations, fp32"
 N_STEPS, ADMM_ITERS, B_PER_GPU, S = 200, 50, 4096, 12
 SM_COUNT, FP32_LANES = 152, 128
+# dram__bytes_read.sum + dram__bytes_write.sum of one fused_kernel<5, step> launch on this
+# workload (profiles/fused_step_paper_4096.md; a 5-step launch of the same kernel -- the state
+# is read once per launch and the grid stays in L2, so the bytes do not grow with the steps)
+TRAFFIC_BYTES = 14_562_304 + 230_656
+TRAFFIC_SOURCE = "ncu capture in profiles/fused_step_paper_4096.md (5-step launch; per-launch bytes)"
 
 
 def flops_per_grasp_step(m: int, n_joints: int, s: int, iters: int) -> float:
@@ -273,7 +278,8 @@ def run_ours(args, rank, world, local_rank):
                    "wrenches": S, "l2": "flushed (256 MB write) before each timed step",
                    "parallelism": f"replicas x{world} (independent grasp shards)"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": TRAFFIC_BYTES if n_up == N_STEPS else None,
+                     "traffic_source": TRAFFIC_SOURCE,
                      "kernel": "fused_kernel<5, step> (one launch per 200-step run)",
                      "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x {sm_max:.0f} MHz",
                      "kernel_ms": float(np.mean(kern_ms)), "alg_flops_per_launch": fl},

@@ -75,9 +75,11 @@ __host__ __device__ constexpr int align4(int v) { return (v + 3) & ~3; }
 template <int M>
 struct Lay {
   static constexpr int NV = 3 * M, NC = 9 * M + 1, NVP = (NV + 3) & ~3;
-  // K^-1 block per grasp; the stride is skewed (== 20 mod 32 words) so that
-  // lanes of two or three grasps in one warp hit disjoint banks.
-  static constexpr int KS = NV * NVP + ((20 - (NV * NVP) % 32) + 32) % 32;
+  // K^-1 block per grasp (packed upper triangle in whole float4s); the
+  // stride is skewed (== 20 mod 32 words) so that lanes of two or three
+  // grasps in one warp hit disjoint banks.
+  static constexpr int KT = 4 * Admm<M>::NTRI4;
+  static constexpr int KS = KT + ((20 - KT % 32) + 32) % 32;
   static constexpr int CTW = 24;  // floats per contact record
   static constexpr int oG = 0;
   static constexpr int oK = oG + 6 * NV;  // K^-1 setup scratch
@@ -418,9 +420,16 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
       const float* ry = per + L::oRY;
       for (int e = lane; e < 6 * NV; e += S) {
         const int r = e / NV, a = e % NV;
-        float s = 0.f;
-        for (int j = 0; j < S; ++j) s = fmaf(ry[j * (6 + NV) + r], ry[j * (6 + NV) + 6 + a], s);
-        per[L::oDG + e] = -2.f * A.w_q * s;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;  // independent partial sums
+        int j = 0;
+        for (; j + 3 < S; j += 4) {
+          s0 = fmaf(ry[j * (6 + NV) + r], ry[j * (6 + NV) + 6 + a], s0);
+          s1 = fmaf(ry[(j + 1) * (6 + NV) + r], ry[(j + 1) * (6 + NV) + 6 + a], s1);
+          s2 = fmaf(ry[(j + 2) * (6 + NV) + r], ry[(j + 2) * (6 + NV) + 6 + a], s2);
+          s3 = fmaf(ry[(j + 3) * (6 + NV) + r], ry[(j + 3) * (6 + NV) + 6 + a], s3);
+        }
+        for (; j < S; ++j) s0 = fmaf(ry[j * (6 + NV) + r], ry[j * (6 + NV) + 6 + a], s0);
+        per[L::oDG + e] = -2.f * A.w_q * ((s0 + s1) + (s2 + s3));
       }
       if (lane == 0) {
         float EQ = 0.f;

@@ -355,6 +355,19 @@ __device__ __forceinline__ void write_G_block(const ContactGeo& k, int i, int nv
   }
 }
 
+// Sizes of one QP with M contacts.
+template <int M>
+struct Admm {
+  static constexpr int NV = 3 * M;
+  static constexpr int NC = 9 * M + 1;
+  static constexpr int NVP = (NV + 3) & ~3;
+  // K^-1 is symmetric: only its upper triangle is stored, row-major and
+  // packed (entry (a, b), a <= b, at tri(a, b)), padded to whole float4s
+  static constexpr int NTRI = NV * (NV + 1) / 2;
+  static constexpr int NTRI4 = (NTRI + 3) / 4;
+  static constexpr __host__ __device__ int tri(int a, int b) { return a * NV - (a * (a - 1)) / 2 + (b - a); }
+};
+
 // ------------------------------------------------------------------ QP setup
 // K = P + sigma I + rho A^T A with P = 2 G^T G (+ 2 eps_reg I).  For the
 // pyramid rows A^T A is the constant
@@ -408,7 +421,7 @@ struct WoodburyScratch {
   static constexpr int floats = (28 + 8 * 3 * M) * (int)(sizeof(R) / 4);
 };
 
-// Writes K^-1 (rows of stride NVP, rounded to float) for one grasp,
+// Writes K^-1 (packed upper triangle, see Admm<M>::tri, rounded to float) for one grasp,
 // computed in precision R: float for the fixed-iteration step loop, double
 // when the solve iterates to a residual target (the ADMM fixed point moves
 // with the backward error of the inverse: the dual residual floor is
@@ -417,7 +430,7 @@ struct WoodburyScratch {
 template <int M, typename R>
 __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const float* G, float* scratch, float* Kinv,
                                            const AdmmCfg& c) {
-  constexpr int NV = 3 * M, NVP = (NV + 3) & ~3;
+  constexpr int NV = 3 * M;
   const DiagK dk = diag_k(c);
   R* Ms = reinterpret_cast<R*>(scratch);  // 28
   R* Us = Ms + 28;                        // NV rows of 8
@@ -449,6 +462,9 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
       }
     }
     const R s2 = sqrt(R(2)), sr = sqrt(R(c.rho));
+    R ild[7];  // reciprocals of the diagonal of L
+#pragma unroll
+    for (int a = 0; a < 7; ++a) ild[a] = R(1) / L[idx(a, a)];
     for (int i = lane; i < NV; i += S) {
       const R id = R(1) / R((i % 3 == 0) ? dk.dn : dk.dt);
       R w[7];
@@ -461,7 +477,7 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
         R t = w[a];
 #pragma unroll
         for (int k = 0; k < a; ++k) t -= L[idx(k, a)] * w[k];
-        w[a] = t / L[idx(a, a)];
+        w[a] = t * ild[a];
       }
 #pragma unroll
       for (int a = 0; a < 7; ++a) Us[i * 8 + a] = w[a];
@@ -474,12 +490,11 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
 #pragma unroll
       for (int a = 0; a < 7; ++a) ui[a] = Us[i * 8 + a];
       const R id = R(1) / R((i % 3 == 0) ? dk.dn : dk.dt);
-#pragma unroll
-      for (int j = 0; j < NV; ++j) {
+      for (int j = i; j < NV; ++j) {
         R t = 0;
 #pragma unroll
         for (int a = 0; a < 7; ++a) t += ui[a] * Us[j * 8 + a];
-        Kinv[i * NVP + j] = (float)((i == j ? id : R(0)) - t);
+        Kinv[Admm<M>::tri(i, j)] = (float)((i == j ? id : R(0)) - t);
       }
     }
   __syncthreads();
@@ -513,12 +528,6 @@ __device__ __forceinline__ float lds32(const float* p) {
   return v;
 }
 
-template <int M>
-struct Admm {
-  static constexpr int NV = 3 * M;
-  static constexpr int NC = 9 * M + 1;
-  static constexpr int NVP = (NV + 3) & ~3;
-};
 
 __device__ constexpr float kFC[8] = {C8, S8, -S8, -C8, -C8, -S8, S8, C8};
 __device__ constexpr float kFS[8] = {S8, C8, C8, S8, -S8, -C8, -C8, -S8};
@@ -544,16 +553,10 @@ __device__ __forceinline__ void At_contact(float v0, const float (&vk)[8], float
 template <int M>
 __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* mq, const float* Kinv,
                                                const AdmmCfg& c) {
-  constexpr int NV = Admm<M>::NV, NVP = Admm<M>::NVP;
-  constexpr int Q4 = NVP / 4;
-  // K^-1 rows are read from shared memory in 16-byte loads; rows 0 and 1
-  // are requested before the rhs is formed, and row a+2 while row a is
-  // used, so that the load latency overlaps arithmetic.
-  float4 k0[Q4], k1[Q4], k2[Q4];
-#pragma unroll
-  for (int q = 0; q < Q4; ++q) k0[q] = lds128(Kinv + 4 * q);
-#pragma unroll
-  for (int q = 0; q < Q4; ++q) k1[q] = lds128(Kinv + NVP + 4 * q);
+  constexpr int NV = Admm<M>::NV, NT4 = Admm<M>::NTRI4, NTRI = Admm<M>::NTRI;
+  // The first float4s of the packed K^-1 are requested before the rhs is
+  // formed; chunk q+2 is requested while chunk q is used.
+  float4 k0 = lds128(Kinv), k1 = lds128(Kinv + 4), k2 = k1;
   // rhs = sigma y - q + rho A^T (2 Pi(w) - w), one contact at a time
   float rhs[NV];
   const float vsum = 2.f * fmaxf(w[9 * M], c.gamma) - w[9 * M];
@@ -569,29 +572,27 @@ __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* 
     rhs[3 * i + 1] = fmaf(c.sigma, y[3 * i + 1], fmaf(c.rho, gd, mq[3 * i + 1]));
     rhs[3 * i + 2] = fmaf(c.sigma, y[3 * i + 2], fmaf(c.rho, ge, mq[3 * i + 2]));
   }
-  // yt = K^-1 rhs
+  // yt = K^-1 rhs from the packed upper triangle: entry (a, b) adds
+  // K_ab rhs_b to yt_a and, off the diagonal, K_ab rhs_a to yt_b.  The
+  // loops unroll completely, so every index below is a compile-time constant.
   float yt[NV];
 #pragma unroll
+  for (int a = 0; a < NV; ++a) yt[a] = 0.f;
+#pragma unroll
   for (int a = 0; a < NV; ++a) {
-    if (a + 2 < NV) {
 #pragma unroll
-      for (int q = 0; q < Q4; ++q) k2[q] = lds128(Kinv + (a + 2) * NVP + 4 * q);
-    }
-    float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-    for (int q = 0; q < Q4; ++q) {
-      const float4 k4 = k0[q];
-      const int b = 4 * q;
-      if (b + 0 < NV) s0 = fmaf(k4.x, rhs[b + 0], s0);
-      if (b + 1 < NV) s1 = fmaf(k4.y, rhs[b + 1], s1);
-      if (b + 2 < NV) s0 = fmaf(k4.z, rhs[b + 2], s0);
-      if (b + 3 < NV) s1 = fmaf(k4.w, rhs[b + 3], s1);
-    }
-    yt[a] = s0 + s1;
-#pragma unroll
-    for (int q = 0; q < Q4; ++q) {
-      k0[q] = k1[q];
-      k1[q] = k2[q];
+    for (int b = a; b < NV; ++b) {
+      const int e = Admm<M>::tri(a, b);
+      const int r = e & 3;
+      const float kv = r == 0 ? k0.x : (r == 1 ? k0.y : (r == 2 ? k0.z : k0.w));
+      yt[a] = fmaf(kv, rhs[b], yt[a]);
+      if (a != b) yt[b] = fmaf(kv, rhs[a], yt[b]);
+      if (r == 3 || e == NTRI - 1) {
+        const int q = e >> 2;
+        if (q + 2 < NT4) k2 = lds128(Kinv + 4 * (q + 2));
+        k0 = k1;
+        k1 = k2;
+      }
     }
   }
   // w <- w + alpha (A yt - Pi(w)),  y <- alpha yt + (1 - alpha) y

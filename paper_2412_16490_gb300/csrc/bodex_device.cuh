@@ -563,9 +563,11 @@ __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* 
 #pragma unroll
   for (int i = 0; i < M; ++i) {
     const float v0 = 2.f * fminf(fmaxf(w[9 * i], 0.f), 1.f) - w[9 * i] + vsum;
+    // facet rows (bounds (-inf, 0]): 2 min(w, 0) - w is exactly -|w|, which
+    // the hardware applies as a free operand modifier
     float vk[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) vk[k] = 2.f * fminf(w[9 * i + 1 + k], 0.f) - w[9 * i + 1 + k];
+    for (int k = 0; k < 8; ++k) vk[k] = -fabsf(w[9 * i + 1 + k]);
     float gn, gd, ge;
     At_contact(v0, vk, c.mu_c8, gn, gd, ge);
     rhs[3 * i] = fmaf(c.sigma, y[3 * i], fmaf(c.rho, gn, mq[3 * i]));

@@ -61,8 +61,10 @@ struct bodex_state_s {
   float* x = nullptr;
   float* am = nullptr;
   float* av = nullptr;
-  float* qy = nullptr;  // [B, s, 3m]
-  float* qw = nullptr;  // [B, s, 9m+1]
+  // ADMM warm start, component-major ([3m][B s] and [9m+1][B s]) so that the
+  // fused kernel's per-step loads and stores are coalesced across lanes
+  float* qy = nullptr;
+  float* qw = nullptr;
   float* res = nullptr;  // [B] max QP residual at the last step of the last launch
   int t = 0;
 };
@@ -287,7 +289,7 @@ struct FusedArgs {
   float* x_state;
   float* am;
   float* av;
-  float* qy;  // warm start, may be null (eval: cold start)
+  float* qy;  // warm start: may be null in eval (cold start); the state's arrays in step mode
   float* qw;
   // outputs
   float* E;
@@ -343,19 +345,21 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
       sc[2] = 0.f;  // max residual of the grasp's QPs at the last step
     }
   }
-  // ADMM warm start of this lane's QP, kept in registers across steps
+  // ADMM iterate of this lane's QP.  In MODE_STEP it lives in the state's
+  // warm-start arrays between upper steps and in registers only around the
+  // solve, so the FK / SDF / adjoint phases get the registers it would hold.
   float y[NV], w[NC];
-  const size_t q = (size_t)b * S + lane;
+  const size_t q = (size_t)b * S + lane, NQ = (size_t)A.B * S;
   if (MODE == MODE_ADJOINT && active) {
 #pragma unroll
     for (int a = 0; a < NV; ++a) y[a] = A.yin[q * NV + a];
 #pragma unroll
     for (int r = 0; r < NC; ++r) w[r] = 0.f;
-  } else if (active && A.qy) {
+  } else if (MODE == MODE_EVAL && active && A.qy) {
 #pragma unroll
-    for (int a = 0; a < NV; ++a) y[a] = A.qy[q * NV + a];
+    for (int a = 0; a < NV; ++a) y[a] = A.qy[a * NQ + q];
 #pragma unroll
-    for (int r = 0; r < NC; ++r) w[r] = A.qw[q * NC + r];
+    for (int r = 0; r < NC; ++r) w[r] = A.qw[r * NQ + q];
   } else {
 #pragma unroll
     for (int a = 0; a < NV; ++a) y[a] = 0.f;
@@ -386,6 +390,12 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
     // ---- A5: ADMM, one QP per lane
     if (active) {
       bool conv = true;
+      if (MODE == MODE_STEP) {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) y[a] = A.qy[a * NQ + q];
+#pragma unroll
+        for (int r = 0; r < NC; ++r) w[r] = A.qw[r * NQ + q];
+      }
       if (MODE != MODE_ADJOINT) {
         float mq[NV];
         neg_q<M>(Gs, t, cfg.beta, mq);
@@ -409,6 +419,12 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
         Q = fmaf(cfg.eps_reg * y[a], y[a], Q);  // regularised value when eps_reg > 0
       }
       per[L::oQ + lane] = Q;
+      if (MODE == MODE_STEP) {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) A.qy[a * NQ + q] = y[a];
+#pragma unroll
+        for (int r = 0; r < NC; ++r) A.qw[r * NQ + q] = w[r];
+      }
       int st = 0;
       if (cfg.eps > 0.f && !conv) st |= BODEX_ST_NOT_CONVERGED;
       if (!isfinite(Q)) st |= BODEX_ST_NONFINITE;
@@ -524,11 +540,11 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
       A.av[(size_t)b * D + k] = avs[k];
     }
   }
-  if (MODE != MODE_ADJOINT && A.qy) {
+  if (MODE == MODE_EVAL && A.qy) {
 #pragma unroll
-    for (int a = 0; a < NV; ++a) A.qy[q * NV + a] = y[a];
+    for (int a = 0; a < NV; ++a) A.qy[a * NQ + q] = y[a];
 #pragma unroll
-    for (int r = 0; r < NC; ++r) A.qw[q * NC + r] = w[r];
+    for (int r = 0; r < NC; ++r) A.qw[r * NQ + q] = w[r];
   }
   if (MODE == MODE_EVAL) {
     if (A.Qout) A.Qout[q] = per[L::oQ + lane];

@@ -421,7 +421,8 @@ struct WoodburyScratch {
   static constexpr int floats = (28 + 8 * 3 * M) * (int)(sizeof(R) / 4);
 };
 
-// Writes K^-1 (packed upper triangle, see Admm<M>::tri, rounded to float) for one grasp,
+// Writes alpha K^-1 (alpha: the ADMM relaxation; packed upper triangle, see
+// Admm<M>::tri; rounded to float) for one grasp,
 // computed in precision R: float for the fixed-iteration step loop, double
 // when the solve iterates to a residual target (the ADMM fixed point moves
 // with the backward error of the inverse: the dual residual floor is
@@ -494,7 +495,7 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
         R t = 0;
 #pragma unroll
         for (int a = 0; a < 7; ++a) t += ui[a] * Us[j * 8 + a];
-        Kinv[Admm<M>::tri(i, j)] = (float)((i == j ? id : R(0)) - t);
+        Kinv[Admm<M>::tri(i, j)] = (float)(R(c.alpha) * ((i == j ? id : R(0)) - t));
       }
     }
   __syncthreads();
@@ -508,6 +509,8 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
 //   yt  = K^-1 rhs,   zt = A yt
 //   y  <- alpha yt + (1 - alpha) y
 //   w  <- w + alpha (zt - Pi(w)).
+// The shared memory holds alpha K^-1, so the product below is alpha yt and
+// the relaxation costs no separate multiply.
 // Row order of A: per contact [f_n, facet 0..7], then the sum row.
 // 16-byte shared-memory load kept inside the loop that issues it.  K^-1 is
 // loop-invariant across ADMM iterations; left to itself the compiler hoists
@@ -554,10 +557,10 @@ template <int M>
 __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* mq, const float* Kinv,
                                                const AdmmCfg& c) {
   constexpr int NV = Admm<M>::NV, NT4 = Admm<M>::NTRI4, NTRI = Admm<M>::NTRI;
-  // The first float4s of the packed K^-1 are requested before the rhs is
-  // formed; chunk q+2 is requested while chunk q is used.
+  // The first float4s of the packed alpha K^-1 are requested before the rhs
+  // is formed; chunk q+2 is requested while chunk q is used.
   float4 k0 = lds128(Kinv), k1 = lds128(Kinv + 4), k2 = k1;
-  // rhs = sigma y - q + rho A^T (2 Pi(w) - w), one contact at a time
+  // rhs = sigma y - q + rho A^T v,  v = 2 Pi(w) - w, one contact at a time
   float rhs[NV];
   const float vsum = 2.f * fmaxf(w[9 * M], c.gamma) - w[9 * M];
 #pragma unroll
@@ -574,7 +577,7 @@ __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* 
     rhs[3 * i + 1] = fmaf(c.sigma, y[3 * i + 1], fmaf(c.rho, gd, mq[3 * i + 1]));
     rhs[3 * i + 2] = fmaf(c.sigma, y[3 * i + 2], fmaf(c.rho, ge, mq[3 * i + 2]));
   }
-  // yt = K^-1 rhs from the packed upper triangle: entry (a, b) adds
+  // yt = alpha K^-1 rhs from the packed upper triangle: entry (a, b) adds
   // K_ab rhs_b to yt_a and, off the diagonal, K_ab rhs_a to yt_b.  The
   // loops unroll completely, so every index below is a compile-time constant.
   float yt[NV];
@@ -597,31 +600,26 @@ __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* 
       }
     }
   }
-  // w <- w + alpha (A yt - Pi(w)),  y <- alpha yt + (1 - alpha) y
+  // w <- w + alpha (A ys - Pi(w)) = (w + A yt) - alpha Pi(w),
+  // y <- alpha ys + (1 - alpha) y = yt + (1 - alpha) y   (yt = alpha ys)
   const float al = c.alpha, bl = 1.0f - c.alpha;
   float sumn = 0.f;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
+    float* wi = w + 9 * i;
     const float tn = yt[3 * i], td = yt[3 * i + 1], te = yt[3 * i + 2];
     sumn += tn;
-    {
-      const float p = fminf(fmaxf(w[9 * i], 0.f), 1.f);
-      w[9 * i] = fmaf(al, tn - p, w[9 * i]);
-    }
+    wi[0] = fmaf(-al, __saturatef(wi[0]), wi[0] + tn);
     const float base = -c.mu_c8 * tn;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
       const float zt = fmaf(kFC[k], td, fmaf(kFS[k], te, base));
-      const float p = fminf(w[9 * i + 1 + k], 0.f);
-      w[9 * i + 1 + k] = fmaf(al, zt - p, w[9 * i + 1 + k]);
+      wi[1 + k] = fmaf(-al, fminf(wi[1 + k], 0.f), wi[1 + k] + zt);
     }
   }
-  {
-    const float p = fmaxf(w[9 * M], c.gamma);
-    w[9 * M] = fmaf(al, sumn - p, w[9 * M]);
-  }
+  w[9 * M] = fmaf(-al, fmaxf(w[9 * M], c.gamma), w[9 * M] + sumn);
 #pragma unroll
-  for (int a = 0; a < NV; ++a) y[a] = fmaf(al, yt[a], bl * y[a]);
+  for (int a = 0; a < NV; ++a) y[a] = fmaf(bl, y[a], yt[a]);
 }
 
 // Infinity-norm residuals at (y, w): primal |A y - z|, dual |P y + q + A^T lam|,

@@ -37,8 +37,14 @@ SM_COUNT, FP32_LANES = 152, 128
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused_kernel<5, step> launch on this
 # workload (profiles/fused_step_paper_4096.md; a 5-step launch of the same kernel -- the state
 # is read once per launch and the grid stays in L2, so the bytes do not grow with the steps)
-TRAFFIC_BYTES = 14_562_304 + 230_656
+TRAFFIC_BYTES = 14_552_320 + 4_864
 TRAFFIC_SOURCE = "ncu capture in profiles/fused_step_paper_4096.md (5-step launch; per-launch bytes)"
+
+
+def admm_iter_flops(m: int) -> int:
+    """Algorithmic FLOPs of one ADMM iteration of one QP (see below)."""
+    nv, nc, nnz = 3 * m, 9 * m + 1, 26 * m
+    return 4 * nnz + 2 * nv * nv + 6 * nv + 10 * nc
 
 
 def flops_per_grasp_step(m: int, n_joints: int, s: int, iters: int) -> float:
@@ -48,8 +54,8 @@ def flops_per_grasp_step(m: int, n_joints: int, s: int, iters: int) -> float:
     nnz(A) = 26 m, nv = 3m, nc = 9m + 1.
     Per grasp and iteration: G^T G 6 nv (nv+1), Cholesky + inverse 2 nv^3,
     FK 72 (6+n), SDF + G 150 m, adjoint 1000, per wrench q, Q and r 24 nv."""
-    nv, nc, nnz = 3 * m, 9 * m + 1, 26 * m
-    f_it = 4 * nnz + 2 * nv * nv + 6 * nv + 10 * nc
+    nv = 3 * m
+    f_it = admm_iter_flops(m)
     setup = 6 * nv * (nv + 1) + 2 * nv ** 3 + 72 * (6 + n_joints) + 150 * m + 1000 + s * 24 * nv
     return s * iters * f_it + setup
 
@@ -258,6 +264,7 @@ def run_ours(args, rank, world, local_rank):
 
     extra = {}
     if rank == 0 and not args.quick:
+        extra["admm_sweep"] = admm_sweep(bx, torch, H, Ob, x_dev, T_dev, P, B)
         extra["qp_solves"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev)
         extra["e2e"] = e2e_rate(bx, torch, H, Ob, st, x0, T_dev, sp)
         extra["persistent_mixed"] = persistent_mixed(bx, torch, P)
@@ -416,6 +423,36 @@ def serving_latency(bx, torch, P, n_jobs):
     return {"arrival_rate_per_s": 20.0, "jobs": n_jobs, "continuous_batching": cont, "plain_per_job": plain,
             "burst_60_jobs": {"continuous_batching": b_cont, "plain_per_job": b_plain},
             "workload_build_s": build_s}
+
+
+def admm_sweep(bx, torch, H, Ob, x_dev, T_dev, P, B, steps=50, iters=(0, 25, 50, 100), reps=4):
+    """Fused-step time (one launch of `steps` upper iterations) against the
+    ADMM iteration count.  The slope is the cost of one ADMM iteration over
+    all B*s QPs; the intercept the per-step setup (FK, SDF, G, K^-1, adjoint,
+    Adam)."""
+    st = bx.State(H, B, S)
+    out = {}
+    for k in iters:
+        sp = bx.step_params(P, qp=bx.qp_params(max_iter=k, eps_abs=0.0))
+        ts = []
+        for r in range(reps):
+            st.set_pose(x_dev)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            bx.bodex_step(H, Ob, st, T_dev, steps, sp)
+            b.record()
+            torch.cuda.synchronize()
+            if r:
+                ts.append(a.elapsed_time(b))
+        out[k] = float(np.median(ts))
+    ks = np.array(iters, float)
+    ms = np.array([out[k] for k in iters])
+    slope, icpt = np.polyfit(ks, ms, 1)
+    us_iter = slope / steps * 1e3
+    return {"upper_steps": steps, "ms_by_admm_iters": {str(k): out[k] for k in iters},
+            "us_per_admm_iter": us_iter, "setup_us_per_upper_step": icpt / steps * 1e3,
+            "admm_tflops": B * S * admm_iter_flops(H.m) / (us_iter * 1e-6) / 1e12}
 
 
 def qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev):

@@ -67,14 +67,22 @@ class _Active:
     nbytes: int
 
 
-def job_bytes(spec: JobSpec) -> int:
-    """Device bytes a job holds while admitted: pose, Adam moments, ADMM warm
-    starts, residual, energy and wrenches (objects are shared, see
-    object_bytes)."""
+def state_bytes(spec: JobSpec) -> int:
+    """Device bytes of the job's optimiser state: pose, Adam moments, ADMM
+    warm starts and residual."""
     B, D = spec.x0.shape
     m, s = spec.hand.n_contacts, spec.T.shape[0]
-    per_grasp = 3 * D + s * (3 * m + 9 * m + 1) + 2
-    return 4 * (B * per_grasp + s * 6)
+    return 4 * B * (3 * D + s * (3 * m + 9 * m + 1) + 1)
+
+
+def job_bytes(spec: JobSpec) -> int:
+    """Device bytes a job holds while admitted: its state, energy and
+    wrenches (objects are shared, see object_bytes)."""
+    return state_bytes(spec) + 4 * (spec.x0.shape[0] + 6 * spec.T.shape[0])
+
+
+def _state_key(spec: JobSpec):
+    return id(spec.hand), spec.x0.shape[0], spec.T.shape[0]
 
 
 def object_bytes(obj) -> int:
@@ -133,11 +141,14 @@ class _Base:
     def result(self, jid: int) -> JobResult:
         return self.results[jid]
 
+    def _new_state(self, spec, hand) -> State:
+        return State(hand, spec.x0.shape[0], spec.T.shape[0])
+
     def _open(self, jid, spec):
         import torch
         hand = self._hand(spec.hand)
         obj = self._object(spec.obj)
-        st = State(hand, spec.x0.shape[0], spec.T.shape[0])
+        st = self._new_state(spec, hand)
         x = torch.as_tensor(np.ascontiguousarray(spec.x0, np.float32)).pin_memory().cuda(non_blocking=True)
         st.set_pose(x)
         T = torch.as_tensor(np.ascontiguousarray(spec.T, np.float32)).cuda()
@@ -179,7 +190,13 @@ class Server(_Base):
     pinned host memory behind that launch and an event recorded; it is
     reported finished (and its memory freed) when the event completes.  At
     most `max_inflight` ticks are queued on the device, so a job that
-    arrives joins within that many ticks."""
+    arrives joins within that many ticks.
+
+    Finished jobs return their optimiser state to a pool keyed by (hand,
+    batch, wrenches) and the next job of that shape reuses it: freeing device
+    memory synchronises the whole device, which would stall the queued
+    ticks.  Pooled states count against the HBM budget; when a job does not
+    fit, pooled states are freed first."""
 
     def __init__(self, params: dict | None = None, qp=None, steps_per_tick: int = 10, hbm_budget: int | None = None,
                  max_jobs: int = BODEX_MAX_JOBS, grasps_per_cta: int = 0, max_inflight: int = 2):
@@ -196,6 +213,8 @@ class Server(_Base):
         self.finishing: list = []   # (job, event, pinned x, pinned E): last tick enqueued
         self.inflight: deque = deque()
         self.used = 0
+        self.pool: dict = {}        # _state_key -> [State]
+        self.pooled = 0             # bytes held by pooled states
         self.launches = 0
         self.peak_active = 0
         self.peak_used = 0
@@ -203,11 +222,33 @@ class Server(_Base):
     def busy(self) -> bool:
         return bool(self.active or self._waiting or self.finishing)
 
+    def _new_state(self, spec, hand) -> State:
+        lst = self.pool.get(_state_key(spec))
+        if lst:
+            self.pooled -= state_bytes(spec)
+            return lst.pop()
+        return super()._new_state(spec, hand)
+
+    def _evict_pool(self, need: int):
+        """Frees pooled states until `need` more bytes fit the budget."""
+        for key in list(self.pool):
+            lst = self.pool[key]
+            while lst and self.used + self.pooled + need > self.hbm_budget:
+                st = lst.pop()
+                self.pooled -= 4 * st.B * (3 * st.D + st.s * (12 * st.m + 1) + 1)
+                del st
+            if not lst:
+                del self.pool[key]
+
     def _admit(self):
         while self._waiting and len(self.active) + len(self.finishing) < self.max_jobs:
             jid, spec = self._waiting[0]
             nb = job_bytes(spec) + (0 if id(spec.obj) in self._objects else object_bytes(spec.obj))
-            if self.used + nb > self.hbm_budget:
+            # a pooled state of the same shape is reused: its bytes are already held
+            reuse = state_bytes(spec) if self.pool.get(_state_key(spec)) else 0
+            if self.used + self.pooled + nb - reuse > self.hbm_budget:
+                self._evict_pool(nb - reuse)
+            if self.used + self.pooled + nb - reuse > self.hbm_budget:
                 if not self.active and not self.finishing and nb > self.hbm_budget:
                     raise MemoryError(f"job {jid} needs {nb} bytes, over the HBM budget {self.hbm_budget}")
                 break  # wait for memory to free up
@@ -217,7 +258,7 @@ class Server(_Base):
             self.active[-1].nbytes = job_bytes(spec)
             self.used += nb
             self.peak_active = max(self.peak_active, len(self.active) + len(self.finishing))
-            self.peak_used = max(self.peak_used, self.used)
+            self.peak_used = max(self.peak_used, self.used + self.pooled)
 
     def _reap(self, block: bool = False):
         keep = []
@@ -228,6 +269,9 @@ class Server(_Base):
                 self.results[a.jid] = JobResult(xh.numpy().copy(), Eh.numpy().copy(), a.spec.arrival, a.start,
                                                 self.now(), a.spec.tag)
                 self.used -= a.nbytes + self._release_object(a.spec.obj)
+                self.pool.setdefault(_state_key(a.spec), []).append(a.state)
+                self.pooled += state_bytes(a.spec)
+                a.state = None
             else:
                 keep.append((a, ev, xh, Eh))
         self.finishing = keep

@@ -296,6 +296,17 @@ int bodex_refine(bodex_hand_t hand, bodex_object_t obj, bodex_state_t state, con
                  float delta, float w_qp, const bodex_step_params* params, float* E_last, int32_t* kstar,
                  int32_t* status, void* stream);
 
+/* Contact Distance Consistency (Sec. V-B): the spread between the largest
+ * and the smallest signed fingertip distance of a grasp.  The signed
+ * distance of fingertip i is the smallest SDF value over its surface samples
+ * (hand desc tip_samples), or phi(c_i) - alpha for a hand without samples.
+ *   x [B,D] (in, device); d [B,m] (out, device, metres); cdc [B] (out,
+ *   device, metres, may be NULL): cdc_b = max_i d_bi - min_i d_bi.
+ * Asynchronous on `stream`; reads nothing but x, the hand and the object.
+ * Errors: BODEX_ERR_INVALID (null handle, B < 0, null x or d), BODEX_ERR_CUDA. */
+int bodex_contact_metrics(bodex_hand_t hand, bodex_object_t obj, const float* x, int B, float* d, float* cdc,
+                          void* stream);
+
 /* Allocation-free variant of bodex_step (the paper has no counterpart: this
  * serves callers that cannot allocate device memory while they run, such as
  * real-time control loops that reserve all memory at start-up, or processes

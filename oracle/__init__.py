@@ -81,6 +81,7 @@ def _sig(L):
                                   _d, _d, _i, _d]
     L.orc_refine_run.argtypes = [_v, _v, _d, _d, _d, C.c_int, _d, C.c_int, C.c_int, C.c_double, C.c_double,
                                  _d, C.c_int, _d]
+    L.orc_contact_metrics.argtypes = [_v, _v, _d, C.c_int, C.c_int, _d, _d]
 
 
 def _p(a, t):
@@ -298,6 +299,16 @@ def refine_eval(hand: Hand, obj: Object, x, p_coarse, delta, w_d, w_qp, threads=
     _load().orc_refine_eval(hand._h, obj._o, _p(x, _d), B, _p(pc, _d), float(delta), float(w_d), float(w_qp),
                             threads or default_threads(), _p(E, _d), _p(g, _d), _p(k, _i), _p(gap, _d))
     return dict(E=E, grad=g, kstar=k, gap=gap)
+
+
+def contact_metrics(hand: Hand, obj: Object, x, threads=None):
+    """Signed fingertip distances d [B,m] and Contact Distance Consistency
+    cdc [B] = max_i d_i - min_i d_i (Sec. V-B), in metres."""
+    x = _f64(x).reshape(-1, hand.D)
+    B = x.shape[0]
+    d, cdc = np.zeros((B, hand.m)), np.zeros(B)
+    _load().orc_contact_metrics(hand._h, obj._o, _p(x, _d), B, threads or default_threads(), _p(d, _d), _p(cdc, _d))
+    return dict(d=d, cdc=cdc)
 
 
 def refine_run(hand: Hand, obj: Object, x, mm, vv, p_coarse, n_steps, t0, delta, w_qp, params, threads=None):

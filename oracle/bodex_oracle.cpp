@@ -1158,6 +1158,38 @@ Refine refine_eval(const Hand& H, const Object& O, const double* x, const double
   return R;
 }
 
+// Contact Distance Consistency (Sec. V-B): the spread between the largest
+// and the smallest signed fingertip distance over the m fingers.  A
+// fingertip's signed distance is the smallest phi over its surface samples
+// (the fine-stage reading of the fingertip surface); a hand without samples
+// uses its coarse sphere, phi(c_i) - alpha.
+struct Metrics {
+  std::vector<double> d;
+  double cdc = 0;
+};
+
+Metrics contact_metrics(const Hand& H, const Object& O, const double* x) {
+  Metrics R;
+  FK f = forward_kinematics(H, x);
+  R.d.assign(H.m, 0.0);
+  for (int i = 0; i < H.m; ++i) {
+    if (H.S > 0) {
+      const Tf T = link_frame(f, H, i);
+      double best = std::numeric_limits<double>::infinity();
+      for (int k = 0; k < H.S; ++k)
+        best = std::min(best, sdf_query(O, tf_apply(T, v3(&H.tips[((size_t)i * H.S + k) * 3]))).phi);
+      R.d[i] = best;
+    } else {
+      R.d[i] = sdf_query(O, f.c[i]).phi - H.alpha;
+    }
+  }
+  if (H.m > 0) {
+    const auto mm = std::minmax_element(R.d.begin(), R.d.end());
+    R.cdc = *mm.second - *mm.first;
+  }
+  return R;
+}
+
 template <class F>
 void parallel_for(int count, int threads, F&& f) {
   threads = std::max(1, std::min(threads, count));
@@ -1458,6 +1490,18 @@ void orc_refine_eval(void* h, void* o, const double* x, int B, const double* pc,
       kstar[(size_t)b * m + i] = R.kstar[i];
       if (gap) gap[(size_t)b * m + i] = R.gap[i];
     }
+  });
+}
+
+// Signed fingertip distances d [B,m] and their spread cdc [B] (Sec. V-B).
+void orc_contact_metrics(void* h, void* o, const double* x, int B, int threads, double* d, double* cdc) {
+  const Hand& H = *static_cast<Hand*>(h);
+  const Object& O = *static_cast<Object*>(o);
+  const int D = 6 + H.n, m = H.m;
+  parallel_for(B, threads, [&](int b) {
+    Metrics R = contact_metrics(H, O, x + (size_t)b * D);
+    for (int i = 0; i < m; ++i) d[(size_t)b * m + i] = R.d[i];
+    cdc[b] = R.cdc;
   });
 }
 

@@ -288,11 +288,24 @@ def bodex_refine(hand: Hand, obj: Object, state: State, p_coarse, n_steps: int, 
     return E_last, kstar, status
 
 
-def synthesize(hand: Hand, obj: Object, x0, T, params: _b.bodex_step_params, coarse_steps=200, fine_steps=50,
-               final_steps=50, margin=0.01, w_qp=1000.0, stream=None):
-    """The three-stage schedule (Sec. IV-D): coarse steps with the QP energy,
-    then fine steps (pre-grasp x_p, margin) and final steps (grasp x), and
-    the squeeze pose x_s = 2 x - x_p.  Returns dict x_p, x, x_s, E."""
+def bodex_contact_metrics(hand: Hand, obj: Object, x, stream=None):
+    """Signed fingertip distances d [B,m] and Contact Distance Consistency
+    cdc [B] = max_i d_i - min_i d_i (Sec. V-B), in metres."""
+    torch = _torch()
+    B = int(x.shape[0])
+    d = torch.empty((B, hand.m), dtype=torch.float32, device=x.device)
+    cdc = torch.empty(B, dtype=torch.float32, device=x.device)
+    _b.check(load().bodex_contact_metrics(hand.handle, obj.handle, _ptr(x), B, _ptr(d), _ptr(cdc), _stream(stream)))
+    return dict(d=d, cdc=cdc)
+
+
+def synthesize(hand: Hand, obj: Object, x0, T, params: _b.bodex_step_params, coarse_steps=300, fine_steps=100,
+               final_steps=100, margin=0.01, w_qp=1000.0, stream=None):
+    """The three-stage schedule (Sec. IV-D; 300 / 100 / 100 iterations):
+    coarse steps with the QP energy, then fine steps (pre-grasp x_p, margin)
+    and final steps (grasp x), and the squeeze pose x_s = 2 x - x_p.
+    Returns dict x_p, x, x_s, E and the grasp's fingertip distances d and
+    Contact Distance Consistency cdc (Sec. V-B)."""
     torch = _torch()
     B = int(x0.shape[0])
     st = State(hand, B, int(T.shape[0]))
@@ -304,7 +317,8 @@ def synthesize(hand: Hand, obj: Object, x0, T, params: _b.bodex_step_params, coa
     xp = st.pose(stream)
     bodex_refine(hand, obj, st, pc, final_steps, 0.0, w_qp, params, E_last=E, stream=stream)
     x = st.pose(stream)
-    return dict(x_p=xp, x=x, x_s=2.0 * x - xp, E=E)
+    met = bodex_contact_metrics(hand, obj, x, stream)
+    return dict(x_p=xp, x=x, x_s=2.0 * x - xp, E=E, d=met["d"], cdc=met["cdc"])
 
 
 def bodex_step_multi(jobs, params: _b.bodex_step_params, stream=None):

@@ -748,6 +748,68 @@ __global__ void __launch_bounds__(RF_LANES * RF_GPB) refine_kernel(RefineArgs A)
   }
 }
 
+// ============================================================================ kernel: contact metrics
+// Contact Distance Consistency (Sec. V-B): d_i = the signed distance of
+// fingertip i, the smallest phi over its surface samples (phi(c_i) - alpha
+// for a hand without samples); cdc = max_i d_i - min_i d_i.  Eight lanes per
+// grasp, lane i < m owns finger i; the spread is reduced across the lanes.
+struct MetricsArgs {
+  const HandDev* hand;
+  const float* tips;  // [m, S, 3] or null
+  ObjDev obj;
+  int B;
+  const float* x;
+  float* d;    // [B, m]
+  float* cdc;  // [B], may be null
+};
+
+template <int M>
+__global__ void __launch_bounds__(RF_LANES * RF_GPB) metrics_kernel(MetricsArgs A) {
+  constexpr int HW = Lay<M>::HAND_WORDS;
+  constexpr int XW = align4(MAXD);
+  __shared__ __align__(16) float smem[HW + RF_GPB * XW];
+  copy_hand_to_smem(A.hand, smem);
+  const int gl = threadIdx.x / RF_LANES, lane = threadIdx.x % RF_LANES;
+  const int b = blockIdx.x * RF_GPB + gl;
+  const bool active = b < A.B;
+  const HandDev& H = *reinterpret_cast<const HandDev*>(smem);
+  float* xs = smem + HW + gl * XW;
+  __syncthreads();
+  const int D = H.D, S = A.tips ? H.S : 0;
+  if (active)
+    for (int k = lane; k < D; k += RF_LANES) xs[k] = A.x[(size_t)b * D + k];
+  __syncthreads();
+  const bool mine = active && lane < M;
+  float d = 0.f;
+  if (mine) {
+    Tf T;
+    fk_link(H, lane, xs, T, nullptr);
+    if (S > 0) {
+      const float* tip = A.tips + (size_t)lane * S * 3;
+      d = INFINITY;
+      for (int k = 0; k < S; ++k) {
+        const float sk[3] = {__ldg(tip + 3 * k), __ldg(tip + 3 * k + 1), __ldg(tip + 3 * k + 2)};
+        float ck[3];
+        tf_point(T, sk, ck);
+        d = fminf(d, sdf_query(A.obj, ck).phi);
+      }
+    } else {
+      float c[3];
+      tf_point(T, H.clocal[lane], c);
+      d = sdf_query(A.obj, c).phi - H.alpha;
+    }
+    A.d[(size_t)b * M + lane] = d;
+  }
+  // spread over the grasp's fingers (all lanes of the 8-lane group take part)
+  float lo = mine ? d : INFINITY, hi = mine ? d : -INFINITY;
+#pragma unroll
+  for (int off = RF_LANES / 2; off >= 1; off >>= 1) {
+    lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off, RF_LANES));
+    hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, off, RF_LANES));
+  }
+  if (active && lane == 0 && A.cdc) A.cdc[b] = hi - lo;
+}
+
 // ============================================================================ host helpers
 namespace {
 
@@ -870,6 +932,13 @@ int run_refine(const RefineArgs& A, cudaStream_t st) {
   (void)cudaGetLastError();
   refine_kernel<M><<<(A.B + RF_GPB - 1) / RF_GPB, RF_LANES * RF_GPB, 0, st>>>(A);
   return launch_err("refine_kernel launch");
+}
+
+template <int M>
+int run_metrics(const MetricsArgs& A, cudaStream_t st) {
+  (void)cudaGetLastError();
+  metrics_kernel<M><<<(A.B + RF_GPB - 1) / RF_GPB, RF_LANES * RF_GPB, 0, st>>>(A);
+  return launch_err("metrics_kernel launch");
 }
 }  // namespace
 
@@ -1362,6 +1431,29 @@ extern "C" int bodex_refine(bodex_hand_t h, bodex_object_t o, bodex_state_t S, c
   }
   if (r == BODEX_OK) S->t += n_steps;
   return r;
+}
+
+extern "C" int bodex_contact_metrics(bodex_hand_t h, bodex_object_t o, const float* x, int B, float* d, float* cdc,
+                                     void* stream) {
+  if (!h || !o) return fail(BODEX_ERR_INVALID, "null handle");
+  if (B < 0) return fail(BODEX_ERR_INVALID, "B < 0");
+  if (B > 0 && (!x || !d)) return fail(BODEX_ERR_INVALID, "null x or d");
+  if (B == 0) return BODEX_OK;
+  MetricsArgs A;
+  std::memset(&A, 0, sizeof(A));
+  A.hand = h->dev;
+  A.tips = (h->host.S > 0) ? h->tips : nullptr;
+  A.obj = o->dev;
+  A.B = B;
+  A.x = x;
+  A.d = d;
+  A.cdc = cdc;
+  switch (h->host.m) {
+    case 3: return run_metrics<3>(A, as_stream(stream));
+    case 4: return run_metrics<4>(A, as_stream(stream));
+    case 5: return run_metrics<5>(A, as_stream(stream));
+    default: return fail(BODEX_ERR_INVALID, "unsupported m");
+  }
 }
 
 // ============================================================================ allocation-free step

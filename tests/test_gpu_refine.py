@@ -64,3 +64,33 @@ def test_synthesize_three_stages():
     ev_p = O.evaluate(O.Hand(hand), O.Object(obj), xp.astype(np.float64), T, P)
     ev_x = O.evaluate(O.Hand(hand), O.Object(obj), x.astype(np.float64), T, P)
     assert np.median(np.abs(ev_x["phi"] - hand.contact_radius)) < np.median(np.abs(ev_p["phi"] - hand.contact_radius)) + 1e-3
+    # the metrics returned with the grasp are those of x
+    ref = O.contact_metrics(O.Hand(hand), O.Object(obj), x.astype(np.float64))
+    np.testing.assert_allclose(host(out["cdc"]), ref["cdc"], rtol=0, atol=4e-6)
+
+
+@pytest.mark.parametrize("kind,B", [("sphere", 64), ("grid", 200)])
+@pytest.mark.parametrize("samples", [True, False])
+def test_contact_metrics_match_oracle(kind, B, samples):
+    """Signed fingertip distances and Contact Distance Consistency (Sec. V-B)
+    vs the FP64 oracle.  The minimum over samples is continuous in the pose,
+    so sample ties do not matter; FP32 chains at 0.1 m give 2e-6 m."""
+    import dataclasses
+    hand, obj, x0, _, _, _ = _case(kind, B)
+    if not samples:
+        hand = dataclasses.replace(hand, tip_samples=None)
+    H, Ob = bx.Hand(hand), bx.Object(obj)
+    out = bx.bodex_contact_metrics(H, Ob, cuda(x0))
+    ref = O.contact_metrics(O.Hand(hand), O.Object(obj), x0.astype(np.float64))
+    np.testing.assert_allclose(host(out["d"]), ref["d"], rtol=0, atol=2e-6)
+    np.testing.assert_allclose(host(out["cdc"]), ref["cdc"], rtol=0, atol=4e-6)
+
+
+def test_contact_metrics_ragged_batch_and_empty():
+    hand, obj, x0, _, _, _ = _case("sphere", 37)  # ragged: 37 grasps over 16-grasp CTAs
+    H, Ob = bx.Hand(hand), bx.Object(obj)
+    out = bx.bodex_contact_metrics(H, Ob, cuda(x0))
+    ref = O.contact_metrics(O.Hand(hand), O.Object(obj), x0.astype(np.float64))
+    np.testing.assert_allclose(host(out["cdc"]), ref["cdc"], rtol=0, atol=4e-6)
+    empty = bx.bodex_contact_metrics(H, Ob, cuda(x0[:0]))
+    assert empty["d"].shape == (0, hand.n_contacts) and empty["cdc"].shape == (0,)

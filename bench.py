@@ -266,6 +266,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.quick:
         extra["admm_sweep"] = admm_sweep(bx, torch, H, Ob, x_dev, T_dev, P, B)
         extra["synthesis"] = synthesis_rate(bx, torch, H, Ob, x_dev, T_dev, sp)
+        extra["energies"] = energy_variants(bx, torch, H, Ob, x_dev, T_dev, P)
         extra["qp_solves"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev)
         extra["e2e"] = e2e_rate(bx, torch, H, Ob, st, x0, T_dev, sp)
         extra["persistent_mixed"] = persistent_mixed(bx, torch, P)
@@ -477,6 +478,33 @@ def synthesis_rate(bx, torch, H, Ob, x_dev, T_dev, sp, reps=2):
             "grasps_per_s": x_dev.shape[0] / (ms / 1e3),
             "cdc_mm_median": float(np.median(cdc_mm)), "cdc_mm_p90": float(np.percentile(cdc_mm, 90)),
             "fingertip_penetration_mm_median": float(np.median(np.maximum(0.0, -d_mm.min(1))))}
+
+
+def energy_variants(bx, torch, H, Ob, x_dev, T_dev, P, reps=3):
+    """The comparison energies of Sec. V-C in the same fused 200-step run:
+    DFC (no QP) and the QP baseline (beta = 0), next to the paper's energy."""
+    B = int(x_dev.shape[0])
+    st = bx.State(H, B, S)
+    E = torch.empty(B, device="cuda")
+    out = {}
+    for name, prm, qp in (("qp_beta1", dict(P), bx.qp_params(max_iter=ADMM_ITERS)),
+                          ("qp_baseline_beta0", dict(P, beta=0.0), bx.qp_params(beta=0.0, max_iter=ADMM_ITERS)),
+                          ("dfc", dict(P, energy=bx.ENERGY_DFC), bx.qp_params(max_iter=ADMM_ITERS))):
+        sp = bx.step_params(prm, qp=qp)
+        ts = []
+        for r in range(reps + 1):
+            st.set_pose(x_dev)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            bx.bodex_step(H, Ob, st, T_dev, N_STEPS, sp, E_last=E)
+            b.record()
+            torch.cuda.synchronize()
+            if r:
+                ts.append(a.elapsed_time(b))
+        ms = float(np.median(ts))
+        out[name] = {"ms": ms, "grasps_per_s": B / (ms / 1e3), "E_last_median": float(E.median().item())}
+    return out
 
 
 def qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev):

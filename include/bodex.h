@@ -154,10 +154,20 @@ typedef struct bodex_qp_params {
 
 /* Energy weights (Sec. IV-C): E = w_q sum_j Q_j + w_d sum_i (phi_i - alpha - delta)^2;
  * delta is the 1 cm pre-grasp margin of Sec. IV-D in the coarse stage. */
+/* Grasp energies.  BODEX_ENERGY_QP: w_q sum_j Q_j, the lower-level QPs of
+ * Eqs. (7)-(9) (with qp.beta = 0 this is the QP baseline of Sec. V-C).
+ * BODEX_ENERGY_DFC: the force-closure energy of DFC (Liu et al. 2021, the
+ * comparison of Sec. V-C): frictionless contacts pushing with equal unit
+ * forces, w_q |sum_i [n_i; p_i x n_i]|^2; no QP is solved (Q and y outputs
+ * are 0).  Both add the distance term w_d sum_i (phi_i - alpha - delta)^2. */
+#define BODEX_ENERGY_QP 0
+#define BODEX_ENERGY_DFC 1
+
 typedef struct bodex_energy_params {
   float w_q;
   float w_d;
   float delta;
+  int kind;  /* BODEX_ENERGY_QP or BODEX_ENERGY_DFC */
 } bodex_energy_params;
 
 /* Upper-level step: Adam (lr_t for the 3 translations, lr_r for all

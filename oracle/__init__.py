@@ -25,7 +25,9 @@ _lock = threading.Lock()
 _lib = None
 
 PARAM_KEYS = ("mu", "beta", "gamma", "w_q", "w_d", "delta", "eps_reg",
-              "lr_t", "lr_r", "b1", "b2", "adam_eps")
+              "lr_t", "lr_r", "b1", "b2", "adam_eps", "energy")
+ENERGY_QP, ENERGY_DFC = 0, 1
+_PARAM_DEFAULTS = {"energy": ENERGY_QP}
 
 
 def build(force: bool = False) -> str:
@@ -148,7 +150,7 @@ class Object:
 
 
 def params_array(params: dict) -> np.ndarray:
-    return np.array([float(params[k]) for k in PARAM_KEYS], np.float64)
+    return np.array([float(params.get(k, _PARAM_DEFAULTS.get(k))) for k in PARAM_KEYS], np.float64)
 
 
 def fk(hand: Hand, x):

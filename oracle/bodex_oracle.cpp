@@ -923,11 +923,26 @@ double qp_bruteforce(const QPProblem& Pb, Vec* ybest) {
 }
 
 // ---------------------------------------------------------------- energy and gradient
+// energy: 0 = the QP grasp energy (Eqs. (7)-(9)); 1 = the DFC force-closure
+// energy of Liu et al. 2021 (the comparison of Sec. V-C), see dfc_wrench.
 struct Params {
   double mu, beta, gamma, w_q, w_d, delta, eps_reg, lr_t, lr_r, b1, b2, adam_eps;
+  int energy;
 };
 Params params_from(const double* a) {
-  return {a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7], a[8], a[9], a[10], a[11]};
+  return {a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7], a[8], a[9], a[10], a[11], (int)a[12]};
+}
+
+// DFC (Liu et al. 2021) assumes frictionless contacts that all push with the
+// same unit force along the inward normal; the grasp is force closure when
+// the resulting net wrench vanishes.  Its energy is |w|^2 with
+//   w = sum_i [n_i; p_i x n_i] = G u,  u = 1 on every normal component.
+void dfc_wrench(const Vec& G, int m, double w[6]) {
+  const int nv = 3 * m;
+  for (int r = 0; r < 6; ++r) {
+    w[r] = 0;
+    for (int i = 0; i < m; ++i) w[r] += G[r * nv + 3 * i];
+  }
 }
 
 struct Eval {
@@ -961,11 +976,17 @@ Eval evaluate(const Hand& H, const Object& O, const double* x, const Params& P, 
   ev.G.assign(6 * 3 * m, 0.0);
   grasp_matrix(m, p.data(), n.data(), O.gc, ev.G.data());
   double EQ = 0;
-  ev.qp.resize(s);
-  for (int j = 0; j < s; ++j) {
-    QPProblem Pb = make_qp(ev.G.data(), m, T + 6 * j, P.mu, P.beta, P.gamma, P.eps_reg);
-    ev.qp[j] = qp_active_set(Pb);
-    EQ += ev.qp[j].Q;
+  if (P.energy == 1) {
+    double w[6];
+    dfc_wrench(ev.G, m, w);
+    for (int r = 0; r < 6; ++r) EQ += w[r] * w[r];
+  } else {
+    ev.qp.resize(s);
+    for (int j = 0; j < s; ++j) {
+      QPProblem Pb = make_qp(ev.G.data(), m, T + 6 * j, P.mu, P.beta, P.gamma, P.eps_reg);
+      ev.qp[j] = qp_active_set(Pb);
+      EQ += ev.qp[j].Q;
+    }
   }
   ev.E = P.w_q * EQ + P.w_d * Ed;
   return ev;
@@ -997,7 +1018,13 @@ void grad_analytic(const Hand& H, const Object& O, const Eval& ev, const Params&
                    double* g) {
   const int m = H.m, nv = 3 * m, D = 6 + H.n;
   Vec dG(6 * nv, 0.0);
-  for (int j = 0; j < s; ++j) {
+  if (P.energy == 1) {  // d|G u|^2 / dG = 2 (G u) u^T
+    double w[6];
+    dfc_wrench(ev.G, m, w);
+    for (int r = 0; r < 6; ++r)
+      for (int i = 0; i < m; ++i) dG[r * nv + 3 * i] = 2.0 * P.w_q * w[r];
+  }
+  for (int j = 0; j < (P.energy == 1 ? 0 : s); ++j) {
     const Vec& y = ev.qp[j].y;
     for (int r = 0; r < 6; ++r) {
       double rr = P.beta * T[6 * j + r];
@@ -1422,7 +1449,7 @@ void orc_evaluate(void* h, void* o, const double* x, int B, const double* params
       if (cell) for (int a = 0; a < 3; ++a) cell[o3 + a] = ev.ct[i].s.cell[a];
     }
     if (G) std::copy(ev.G.begin(), ev.G.end(), G + (size_t)b * 6 * nv);
-    for (int j = 0; j < s; ++j) {
+    for (int j = 0; j < (int)ev.qp.size(); ++j) {  // no QPs under the DFC energy
       if (Q) Q[(size_t)b * s + j] = ev.qp[j].Q;
       if (y) std::copy(ev.qp[j].y.begin(), ev.qp[j].y.end(), y + ((size_t)b * s + j) * nv);
       if (unique) unique[(size_t)b * s + j] = ev.qp[j].unique;

@@ -14,7 +14,7 @@ import ctypes as C
 import numpy as np
 
 from . import _binding as _b
-from ._binding import BodexError, ST_DEGENERATE_NORMAL, ST_NONFINITE, ST_NOT_CONVERGED  # noqa: F401
+from ._binding import BodexError, ENERGY_DFC, ENERGY_QP, ST_DEGENERATE_NORMAL, ST_NONFINITE, ST_NOT_CONVERGED  # noqa: F401
 
 __all__ = [
     "load", "Hand", "Object", "State", "qp_params", "step_params",
@@ -66,16 +66,17 @@ def qp_params(mu=0.5, beta=1.0, gamma=0.5, rho=0.1, sigma=1e-6, alpha=1.6, eps_a
 def step_params(params: dict | None = None, qp: _b.bodex_qp_params | None = None,
                 grasps_per_cta: int = 0) -> _b.bodex_step_params:
     """Upper-level parameters (struct bodex_step_params) from a dict with keys
-    lr_t, lr_r, b1, b2, adam_eps, w_q, w_d, delta (and mu, beta, gamma, eps_reg
-    used when `qp` is not given)."""
+    lr_t, lr_r, b1, b2, adam_eps, w_q, w_d, delta, energy (ENERGY_QP or
+    ENERGY_DFC; and mu, beta, gamma, eps_reg used when `qp` is not given)."""
     p = dict(lr_t=2e-3, lr_r=2e-2, b1=0.9, b2=0.999, adam_eps=1e-8, w_q=1.0, w_d=1000.0, delta=0.01,
-             mu=0.5, beta=1.0, gamma=0.5, eps_reg=0.0)
+             mu=0.5, beta=1.0, gamma=0.5, eps_reg=0.0, energy=_b.ENERGY_QP)
     if params:
         p.update({k: v for k, v in params.items() if k in p})
     if qp is None:
         qp = qp_params(mu=p["mu"], beta=p["beta"], gamma=p["gamma"], eps_reg=p["eps_reg"])
     return _b.bodex_step_params(p["lr_t"], p["lr_r"], p["b1"], p["b2"], p["adam_eps"],
-                                _b.bodex_energy_params(p["w_q"], p["w_d"], p["delta"]), qp, int(grasps_per_cta))
+                                _b.bodex_energy_params(p["w_q"], p["w_d"], p["delta"], int(p["energy"])), qp,
+                                int(grasps_per_cta))
 
 
 # ---------------------------------------------------------------- handles

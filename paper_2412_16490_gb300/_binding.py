@@ -26,6 +26,8 @@ ST_NOT_CONVERGED = 2
 ST_DEGENERATE_NORMAL = 4
 
 # Every symbol include/bodex.h declares (checked by the CPU test-suite).
+ENERGY_QP, ENERGY_DFC = 0, 1
+
 EXPORTS = (
     "bodex_hand_create", "bodex_hand_destroy", "bodex_object_create", "bodex_object_destroy",
     "bodex_object_gravity_centre", "bodex_fk_contacts", "bodex_qp_solve_batch", "bodex_state_create",
@@ -54,7 +56,7 @@ class bodex_qp_params(C.Structure):
 
 
 class bodex_energy_params(C.Structure):
-    _fields_ = [("w_q", C.c_float), ("w_d", C.c_float), ("delta", C.c_float)]
+    _fields_ = [("w_q", C.c_float), ("w_d", C.c_float), ("delta", C.c_float), ("kind", C.c_int)]
 
 
 class bodex_step_params(C.Structure):

@@ -300,6 +300,7 @@ struct FusedArgs {
   const float* yin;  // MODE_ADJOINT: forces from a previous solve [B, s, 3m]
   float* res;        // [B] max ADMM residual of the grasp's QPs at the last step (may be null)
   int gpb;           // grasps per CTA
+  int dfc;           // 1: the DFC force-closure energy |G u|^2 replaces the QPs (uniform per launch)
 };
 
 // MODE_EVAL: E and dE/dx at x.  MODE_STEP: n_steps upper iterations on the
@@ -386,9 +387,10 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
     }
     __syncthreads();
     // ---- A4: K^-1 per grasp
-    if (MODE != MODE_ADJOINT) setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg);
+    if (MODE != MODE_ADJOINT && !A.dfc) setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg);
     // ---- A5: ADMM, one QP per lane
-    if (active) {
+    if (active && A.dfc) per[L::oQ + lane] = 0.f;  // no lower-level QPs under DFC
+    if (active && !A.dfc) {
       bool conv = true;
       if (MODE == MODE_STEP) {
 #pragma unroll
@@ -432,7 +434,37 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
     }
     __syncthreads();
     // ---- A6: energy;  A7 (part 1): dE/dG = -2 w_Q sum_j r_j y_j^T
-    if (active) {
+    // (DFC: E_Q = |G u|^2 with u = 1 on every normal component, so
+    // dE/dG = 2 w_Q (G u) u^T: only the normal columns)
+    if (active && A.dfc) {
+      float gu[6];
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < M; ++i) s += Gs[r * NV + 3 * i];
+        gu[r] = s;
+      }
+      for (int e = lane; e < 6 * NV; e += S) {
+        const int r = e / NV, a = e % NV;
+        float g = 0.f;
+#pragma unroll
+        for (int rr = 0; rr < 6; ++rr) g = (rr == r) ? gu[rr] : g;
+        per[L::oDG + e] = (a % 3 == 0) ? 2.f * A.w_q * g : 0.f;
+      }
+      if (lane == 0) {
+        float EQ = 0.f;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) EQ = fmaf(gu[r], gu[r], EQ);
+        float Ed = 0.f;
+        for (int i = 0; i < M; ++i) {
+          const float r = per[L::oCT + L::CTW * i + 9] - H.alpha - A.delta;
+          Ed = fmaf(r, r, Ed);
+        }
+        sc[0] = A.w_q * EQ + A.w_d * Ed;
+      }
+    }
+    if (active && !A.dfc) {
       const float* ry = per + L::oRY;
       for (int e = lane; e < 6 * NV; e += S) {
         const int r = e / NV, a = e % NV;
@@ -1261,6 +1293,9 @@ static int fill_args(FusedArgs& A, bodex_hand_t h, bodex_object_t o, const float
   // error of K^-1: build it in double there
   A.cfg.fp64_setup = (p->qp.eps_abs > 0.f && p->qp.eps_abs <= 2e-6f) ? 1 : 0;
   A.gpb = p->grasps_per_cta;
+  if (p->energy.kind != BODEX_ENERGY_QP && p->energy.kind != BODEX_ENERGY_DFC)
+    return fail(BODEX_ERR_INVALID, "energy.kind must be BODEX_ENERGY_QP or BODEX_ENERGY_DFC");
+  A.dfc = p->energy.kind == BODEX_ENERGY_DFC;
   return BODEX_OK;
 }
 

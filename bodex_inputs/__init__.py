@@ -61,6 +61,11 @@ class HandTemplate:
     contact_local: np.ndarray   # [m, 3] float32
     contact_radius: float       # alpha, the fingertip sphere radius (m)
     tip_samples: np.ndarray = field(default=None)  # [m, S, 3] float32
+    # collision spheres (cuRobo-style hand geometry): link (-1 = palm/root),
+    # centre in that link's frame, radius
+    sphere_link: np.ndarray = field(default=None)    # [K] int32
+    sphere_local: np.ndarray = field(default=None)   # [K, 3] float32
+    sphere_radius: np.ndarray = field(default=None)  # [K] float32
 
     @property
     def n_joints(self) -> int:
@@ -122,8 +127,36 @@ class _Builder:
         self.clink.append(prev)
         self.clocal.append((0.0, tip, 0.0))
 
-    def build(self, name, radius, n_tip_samples=32):
+    def spheres(self, radius, palm):
+        """Collision spheres: along every finger link (the +y segment from the
+        joint to the next joint, or to the fingertip contact, which keeps its
+        own sphere out) at a spacing of 1.5 radii, plus the palm spheres
+        ``palm`` = [(x, y, z, r)] on the root."""
         n = len(self.parent)
+        link, local, rad = [], [], []
+        for x, y, z, r in palm:
+            link.append(-1)
+            local.append((x, y, z))
+            rad.append(r)
+        step = 1.5 * radius
+        for j in range(n):
+            kids = [c for c in range(n) if self.parent[c] == j]
+            if kids:
+                L = float(np.asarray(self.offset[kids[0]]).reshape(3, 4)[1, 3])
+            else:
+                L = float(self.clocal[self.clink.index(j)][1])
+            k = 0
+            while k * step < L - 0.5 * step:
+                link.append(j)
+                local.append((0.0, k * step, 0.0))
+                rad.append(radius)
+                k += 1
+        return (np.array(link, np.int32), np.array(local, np.float32).reshape(-1, 3),
+                np.array(rad, np.float32))
+
+    def build(self, name, radius, n_tip_samples=32, palm=()):
+        n = len(self.parent)
+        sl, sp, sr = self.spheres(radius, palm)
         vlo = [-0.3, -0.3, -0.3, -math.pi, -math.pi, -math.pi]
         vhi = [0.3, 0.3, 0.3, math.pi, math.pi, math.pi]
         clocal = np.array(self.clocal, float)
@@ -139,10 +172,21 @@ class _Builder:
             contact_local=clocal.astype(np.float32),
             contact_radius=float(radius),
             tip_samples=samples.astype(np.float32),
+            sphere_link=sl,
+            sphere_local=sp,
+            sphere_radius=sr,
         )
 
 
 X, Y, Z = (1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0)
+
+
+def _palm(nx, ny, dx, ys, r):
+    """nx x ny palm spheres of radius r centred r/2 under the palm plane."""
+    xs = [(k - (nx - 1) / 2) * dx for k in range(nx)]
+    y0, y1 = ys
+    yy = [y0 + (y1 - y0) * k / max(1, ny - 1) for k in range(ny)]
+    return [(x, y, -0.5 * r, r) for y in yy for x in xs]
 HAND_NAMES = ("hand4", "hand3", "hand4x4", "hand5")
 
 
@@ -163,18 +207,18 @@ def hand_template(name: str) -> HandTemplate:
         for xb in (-0.02, 0.0, 0.02):
             b.finger((xb, 0.03), 0.0, [flex(0.0), flex(0.04), flex(0.03)], 0.025)
         b.finger((0.0, -0.03), math.pi, [flex(0.0), flex(0.04), flex(0.03)], 0.025)
-        return b.build(name, 0.008)
+        return b.build(name, 0.008, palm=_palm(3, 2, 0.02, (-0.01, 0.015), 0.011))
     if name == "hand3":
         for xb in (-0.02, 0.02):
             b.finger((xb, 0.03), 0.0, [flex(0.0), flex(0.04), flex(0.03)], 0.025)
         b.finger((0.0, -0.03), math.pi, [flex(0.0), flex(0.04), flex(0.03)], 0.025)
-        return b.build(name, 0.008)
+        return b.build(name, 0.008, palm=_palm(2, 2, 0.02, (-0.01, 0.015), 0.011))
     if name == "hand4x4":
         abd = (Z, 0.0, -20 * DEG, 20 * DEG)
         for xb in (-0.02, 0.0, 0.02):
             b.finger((xb, 0.03), 0.0, [abd, flex(0.0), flex(0.04), flex(0.03)], 0.025)
         b.finger((0.0, -0.03), math.pi, [abd, flex(0.0), flex(0.04), flex(0.03)], 0.025)
-        return b.build(name, 0.008)
+        return b.build(name, 0.008, palm=_palm(3, 2, 0.02, (-0.01, 0.015), 0.011))
     if name == "hand5":
         abd = (Z, 0.0, -20 * DEG, 20 * DEG)
         fl = lambda L, lo=0.0: (X, L, lo * DEG, 90 * DEG)
@@ -188,7 +232,7 @@ def hand_template(name: str) -> HandTemplate:
         b.finger((-0.025, -0.015), math.pi,
                  [(Y, 0.0, -60 * DEG, 60 * DEG), (Z, 0.0, -30 * DEG, 30 * DEG),
                   fl(0.0, -15), fl(0.038), fl(0.032)], 0.027)
-        return b.build(name, 0.009)
+        return b.build(name, 0.009, palm=_palm(3, 2, 0.022, (-0.005, 0.02), 0.012))
     raise ValueError(f"unknown hand template {name!r}")
 
 

@@ -25,9 +25,11 @@ _lock = threading.Lock()
 _lib = None
 
 PARAM_KEYS = ("mu", "beta", "gamma", "w_q", "w_d", "delta", "eps_reg",
-              "lr_t", "lr_r", "b1", "b2", "adam_eps", "energy")
+              "lr_t", "lr_r", "b1", "b2", "adam_eps", "energy",
+              "w_pen", "w_self", "w_lim", "eta_pen", "eta_lim")
 ENERGY_QP, ENERGY_DFC = 0, 1
-_PARAM_DEFAULTS = {"energy": ENERGY_QP}
+_PARAM_DEFAULTS = {"energy": ENERGY_QP, "w_pen": 0.0, "w_self": 0.0, "w_lim": 0.0, "eta_pen": 0.005,
+                   "eta_lim": 0.0}
 
 
 def build(force: bool = False) -> str:
@@ -57,7 +59,10 @@ _v = C.c_void_p
 
 def _sig(L):
     L.orc_hand_new.restype = _v
-    L.orc_hand_new.argtypes = [C.c_int, C.c_int, _i, _f, _f, _f, _f, _i, _f, C.c_double, C.c_int, _f]
+    L.orc_hand_new.argtypes = [C.c_int, C.c_int, _i, _f, _f, _f, _f, _i, _f, C.c_double, C.c_int, _f,
+                               C.c_int, _i, _f, _f]
+    L.orc_hand_pairs.restype = C.c_int
+    L.orc_hand_pairs.argtypes = [_v, _i]
     L.orc_hand_free.argtypes = [_v]
     L.orc_object_sphere.restype = _v
     L.orc_object_sphere.argtypes = [C.c_double] * 4
@@ -116,9 +121,21 @@ class Hand:
         tips = tpl.tip_samples
         S = 0 if tips is None else int(tips.shape[1])
         tips = _f32(tips) if tips is not None else None
+        sl = getattr(tpl, "sphere_link", None)
+        K = 0 if sl is None else int(len(sl))
+        sph = [np.ascontiguousarray(sl, np.int32), _f32(tpl.sphere_local), _f32(tpl.sphere_radius)] if K else [None] * 3
+        self.K = K
         self._h = L.orc_hand_new(self.n, self.m, _p(keep[0], _i), _p(keep[1], _f), _p(keep[2], _f),
                                  _p(keep[3], _f), _p(keep[4], _f), _p(keep[5], _i), _p(keep[6], _f),
-                                 float(tpl.contact_radius), S, _p(tips, _f))
+                                 float(tpl.contact_radius), S, _p(tips, _f), K, _p(sph[0], _i), _p(sph[1], _f),
+                                 _p(sph[2], _f))
+
+    def pairs(self) -> np.ndarray:
+        """Self-collision sphere pairs [P, 2] (spheres on non-neighbouring links)."""
+        n = _load().orc_hand_pairs(self._h, None)
+        out = np.zeros((n, 2), np.int32)
+        _load().orc_hand_pairs(self._h, _p(out, _i))
+        return out
 
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:

@@ -121,6 +121,12 @@ struct Hand {
   Vec offset, axis, qmin, qmax, clocal, tips;
   double alpha = 0;
   std::vector<std::vector<char>> anc;  // anc[i][j]: joint j (of 6+n) moves contact i
+  // collision spheres: link (-1 = root), centre in the link frame, radius;
+  // pairs checked for self-penetration (see build_pairs)
+  int K = 0;
+  std::vector<int> slink;
+  Vec slocal, srad;
+  std::vector<std::pair<int, int>> pairs;
 };
 
 struct Object {
@@ -141,6 +147,7 @@ struct Object {
 // prismatic joints along the world axes followed by three revolute joints
 // about X, then Y, then Z (intrinsic):  T_root = Trans(t) Rx Ry Rz.
 struct FK {
+  Tf root;                 // root frame T_root
   std::vector<Tf> T;       // [n] joint frames (after the joint's own rotation)
   std::vector<V3> c;       // [m] contact points in the world
   std::vector<V3> omega;   // [6+n] joint axis in the world (unit, prismatic: direction)
@@ -159,6 +166,7 @@ FK forward_kinematics(const Hand& H, const double* x) {
   const Tf Rz = tf_rot({0, 0, 1}, x[5]);
   const Tf Rxy = tf_mul(Rx, Ry);
   const Tf root = tf_mul(tf_trans(t.x, t.y, t.z), tf_mul(Rxy, Rz));
+  out.root = root;
   out.omega[0] = {1, 0, 0};
   out.omega[1] = {0, 1, 0};
   out.omega[2] = {0, 0, 1};
@@ -928,9 +936,11 @@ double qp_bruteforce(const QPProblem& Pb, Vec* ybest) {
 struct Params {
   double mu, beta, gamma, w_q, w_d, delta, eps_reg, lr_t, lr_r, b1, b2, adam_eps;
   int energy;
+  double w_pen, w_self, w_lim, eta_pen, eta_lim;  // collision energies (collision_energy)
 };
 Params params_from(const double* a) {
-  return {a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7], a[8], a[9], a[10], a[11], (int)a[12]};
+  return {a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7], a[8], a[9], a[10], a[11], (int)a[12],
+          a[13], a[14], a[15], a[16], a[17]};
 }
 
 // DFC (Liu et al. 2021) assumes frictionless contacts that all push with the
@@ -946,6 +956,7 @@ void dfc_wrench(const Vec& G, int m, double w[6]) {
 }
 
 struct Eval {
+  Vec x;
   FK fk;
   std::vector<Contact> ct;
   Vec G;
@@ -958,8 +969,110 @@ struct Eval {
 // Distance-energy reading: the paper's coarse term is (|c - p| - alpha)^2
 // (Sec. IV-C); the signed SDF value replaces |c - p| so that penetration is
 // penalised, and delta is the pre-grasp margin (Sec. IV-D).
+// ---------------------------------------------------------------- collision energies
+// The constraints of Eq. (4) (joint limits) and "no hand-hand / hand-object
+// collision", as cuRobo-style energies on the hand's collision spheres
+// (Sec. IV-B).  Readings:
+//   penetration  E_pen  = w_pen sum_s h(r_s + eta_pen - phi(c_s)), with the
+//                h(p) = 0 (p <= 0), p^2 / (2 eta) (0 < p <= eta), p - eta/2
+//                (p > eta), a quadratic-then-linear hinge (eta = 0: max(p, 0));
+//   self         E_self = w_self sum_{(a,b) in pairs} max(0, r_a + r_b - |c_a - c_b|)^2;
+//   joint limits E_lim  = w_lim sum_{k >= 6} max(0, x_k - x_max,k + eta_lim)^2
+//                                          + max(0, x_min,k + eta_lim - x_k)^2.
+// Pairs: spheres on different links, except a link and its nearest
+// ancestor link that carries spheres (the root counts as such an ancestor),
+// which touch by construction (neighbouring links).
+void build_pairs(Hand& H) {
+  std::vector<char> has(H.n, 0);
+  for (int s = 0; s < H.K; ++s)
+    if (H.slink[s] >= 0) has[H.slink[s]] = 1;
+  auto eff_parent = [&](int L) {  // -1: the root; -2: none (L is the root)
+    if (L < 0) return -2;
+    int p = H.parent[L];
+    while (p >= 0 && !has[p]) p = H.parent[p];
+    return p;
+  };
+  H.pairs.clear();
+  for (int a = 0; a < H.K; ++a)
+    for (int b = a + 1; b < H.K; ++b) {
+      const int la = H.slink[a], lb = H.slink[b];
+      if (la == lb || eff_parent(la) == lb || eff_parent(lb) == la) continue;
+      H.pairs.emplace_back(a, b);
+    }
+}
+
+bool moves(const Hand& H, int jx, int link) {  // does joint jx (of 6+n) move `link`?
+  if (jx < 6) return true;
+  for (int j = link; j >= 0; j = H.parent[j])
+    if (j == jx - 6) return true;
+  return false;
+}
+
+double penetration_hinge(double p, double eta, double* dh) {
+  if (p <= 0) {
+    *dh = 0;
+    return 0;
+  }
+  if (eta > 0 && p <= eta) {
+    *dh = p / eta;
+    return p * p / (2 * eta);
+  }
+  *dh = 1;
+  return p - 0.5 * eta;
+}
+
+// E_pen + E_self + E_lim at x (frames f); adds the gradient to g when given.
+double collision_energy(const Hand& H, const Object& O, const FK& f, const double* x, const Params& P, double* g) {
+  const int D = 6 + H.n;
+  double E = 0;
+  std::vector<V3> c(H.K), dc(H.K, V3{0, 0, 0});
+  for (int s = 0; s < H.K; ++s)
+    c[s] = tf_apply(H.slink[s] < 0 ? f.root : f.T[H.slink[s]], v3(&H.slocal[3 * s]));
+  if (P.w_pen != 0)
+    for (int s = 0; s < H.K; ++s) {
+      const SdfOut q = sdf_query(O, c[s]);
+      double dh;
+      E += P.w_pen * penetration_hinge(H.srad[s] + P.eta_pen - q.phi, P.eta_pen, &dh);
+      dc[s] = dc[s] - (P.w_pen * dh) * V3{q.g[0], q.g[1], q.g[2]};
+    }
+  if (P.w_self != 0)
+    for (const auto& pr : H.pairs) {
+      const V3 v = c[pr.first] - c[pr.second];
+      const double L = std::sqrt(dot(v, v));
+      const double d = H.srad[pr.first] + H.srad[pr.second] - L;
+      if (d <= 0) continue;
+      E += P.w_self * d * d;
+      const V3 u = (1.0 / L) * v;
+      dc[pr.first] = dc[pr.first] - (2 * P.w_self * d) * u;
+      dc[pr.second] = dc[pr.second] + (2 * P.w_self * d) * u;
+    }
+  if (P.w_lim != 0)
+    for (int k = 6; k < D; ++k) {
+      const double hi = x[k] - H.qmax[k] + P.eta_lim, lo = H.qmin[k] + P.eta_lim - x[k];
+      if (hi > 0) {
+        E += P.w_lim * hi * hi;
+        if (g) g[k] += 2 * P.w_lim * hi;
+      }
+      if (lo > 0) {
+        E += P.w_lim * lo * lo;
+        if (g) g[k] -= 2 * P.w_lim * lo;
+      }
+    }
+  if (g)
+    for (int s = 0; s < H.K; ++s)
+      for (int jx = 0; jx < D; ++jx) {
+        if (!moves(H, jx, H.slink[s])) continue;
+        const V3 d = jx < 3 ? f.omega[jx] : cross(f.omega[jx], c[s] - f.org[jx]);
+        g[jx] += dot(dc[s], d);
+      }
+  return E;
+}
+
+bool has_collision_terms(const Params& P) { return P.w_pen != 0 || P.w_self != 0 || P.w_lim != 0; }
+
 Eval evaluate(const Hand& H, const Object& O, const double* x, const Params& P, const double* T, int s) {
   Eval ev;
+  ev.x.assign(x, x + 6 + H.n);
   ev.fk = forward_kinematics(H, x);
   const int m = H.m;
   ev.ct.resize(m);
@@ -989,6 +1102,7 @@ Eval evaluate(const Hand& H, const Object& O, const double* x, const Params& P, 
     }
   }
   ev.E = P.w_q * EQ + P.w_d * Ed;
+  if (has_collision_terms(P)) ev.E += collision_energy(H, O, ev.fk, x, P, nullptr);
   return ev;
 }
 
@@ -1096,6 +1210,7 @@ void grad_analytic(const Hand& H, const Object& O, const Eval& ev, const Params&
       g[jx] += dot(gc, dc);
     }
   }
+  if (has_collision_terms(P)) collision_energy(H, O, ev.fk, ev.x.data(), P, g);
 }
 
 // One Adam step (Kingma & Ba 2015) on x, then clamp to [x_min, x_max]
@@ -1239,7 +1354,7 @@ extern "C" {
 
 void* orc_hand_new(int n, int m, const int32_t* parent, const float* offset, const float* axis, const float* qmin,
                    const float* qmax, const int32_t* clink, const float* clocal, double alpha, int S,
-                   const float* tips) {
+                   const float* tips, int K, const int32_t* slink, const float* slocal, const float* srad) {
   Hand* H = new Hand();
   H->n = n;
   H->m = m;
@@ -1254,6 +1369,13 @@ void* orc_hand_new(int n, int m, const int32_t* parent, const float* offset, con
   if (S > 0 && tips) H->tips.assign(tips, tips + 3 * (size_t)m * S);
   H->alpha = alpha;
   build_ancestors(*H);
+  H->K = (K > 0 && slink && slocal && srad) ? K : 0;
+  if (H->K > 0) {
+    H->slink.assign(slink, slink + K);
+    H->slocal.assign(slocal, slocal + 3 * (size_t)K);
+    H->srad.assign(srad, srad + K);
+  }
+  build_pairs(*H);
   return H;
 }
 void orc_hand_free(void* h) { delete static_cast<Hand*>(h); }
@@ -1518,6 +1640,17 @@ void orc_refine_eval(void* h, void* o, const double* x, int B, const double* pc,
       if (gap) gap[(size_t)b * m + i] = R.gap[i];
     }
   });
+}
+
+// Self-collision pairs of the hand (build_pairs): count, and [count,2] when out is given.
+int orc_hand_pairs(void* h, int32_t* out) {
+  const Hand& H = *static_cast<Hand*>(h);
+  if (out)
+    for (size_t k = 0; k < H.pairs.size(); ++k) {
+      out[2 * k] = H.pairs[k].first;
+      out[2 * k + 1] = H.pairs[k].second;
+    }
+  return (int)H.pairs.size();
 }
 
 // Signed fingertip distances d [B,m] and their spread cdc [B] (Sec. V-B).

@@ -482,14 +482,19 @@ def synthesis_rate(bx, torch, H, Ob, x_dev, T_dev, sp, reps=2):
 
 def energy_variants(bx, torch, H, Ob, x_dev, T_dev, P, reps=3):
     """The comparison energies of Sec. V-C in the same fused 200-step run:
-    DFC (no QP) and the QP baseline (beta = 0), next to the paper's energy."""
+    DFC (no QP) and the QP baseline (beta = 0), next to the paper's energy;
+    and the paper's energy with the collision-sphere constraint energies of
+    Sec. IV-B (penetration, self-penetration, joint limits) switched on."""
     B = int(x_dev.shape[0])
     st = bx.State(H, B, S)
     E = torch.empty(B, device="cuda")
     out = {}
     for name, prm, qp in (("qp_beta1", dict(P), bx.qp_params(max_iter=ADMM_ITERS)),
                           ("qp_baseline_beta0", dict(P, beta=0.0), bx.qp_params(beta=0.0, max_iter=ADMM_ITERS)),
-                          ("dfc", dict(P, energy=bx.ENERGY_DFC), bx.qp_params(max_iter=ADMM_ITERS))):
+                          ("dfc", dict(P, energy=bx.ENERGY_DFC), bx.qp_params(max_iter=ADMM_ITERS)),
+                          ("qp_beta1_with_collision_energies",
+                           dict(P, w_pen=100.0, w_self=100.0, w_lim=10.0, eta_pen=0.005, eta_lim=0.05),
+                           bx.qp_params(max_iter=ADMM_ITERS))):
         sp = bx.step_params(prm, qp=qp)
         ts = []
         for r in range(reps + 1):

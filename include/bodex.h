@@ -64,6 +64,7 @@ extern "C" {
 #define BODEX_MAX_CONTACTS 5  /* m in {3, 4, 5} are compiled */
 #define BODEX_MAX_CHAIN 8     /* joints between the root and a contact link */
 #define BODEX_MAX_JOBS 64     /* jobs per bodex_step_multi launch */
+#define BODEX_MAX_SPHERES 48  /* collision spheres per hand */
 
 typedef struct bodex_hand_s* bodex_hand_t;
 typedef struct bodex_object_s* bodex_object_t;
@@ -91,6 +92,16 @@ typedef struct bodex_hand_desc {
   float contact_radius;        /* alpha, sphere radius (m) */
   int n_tip_samples;           /* S for the refinement epilogue, 0 if unused */
   const float* tip_samples;    /* [m,S,3] fingertip surface samples, link frame */
+  /* Collision spheres for the penetration and self-penetration energies
+   * (0..BODEX_MAX_SPHERES; 0 if unused).  Sphere k sits on link
+   * sphere_link[k] (-1 = the root/palm frame) at sphere_local[k] with radius
+   * sphere_radius[k] > 0.  Self-penetration pairs are all spheres on
+   * different links except a link and its nearest ancestor link that
+   * carries spheres (the root counts), which touch by construction. */
+  int n_spheres;
+  const int32_t* sphere_link;  /* [K] */
+  const float* sphere_local;   /* [K,3] */
+  const float* sphere_radius;  /* [K] */
 } bodex_hand_desc;
 
 /* Copies the template to the device.  Errors: BODEX_ERR_INVALID for sizes
@@ -163,11 +174,21 @@ typedef struct bodex_qp_params {
 #define BODEX_ENERGY_QP 0
 #define BODEX_ENERGY_DFC 1
 
+/* Upper-level constraint energies in the style of cuRobo (Sec. IV-B: joint
+ * limits, Eq. (4), and no hand-hand / hand-object collision), on the hand's
+ * collision spheres (c_k, r_k), all off at weight 0:
+ *   w_pen  sum_k h(r_k + eta_pen - phi(c_k)),  h(p) = 0 (p <= 0),
+ *          p^2 / (2 eta_pen) (0 < p <= eta_pen), p - eta_pen / 2 (p > eta_pen);
+ *   w_self sum_pairs max(0, r_a + r_b - |c_a - c_b|)^2;
+ *   w_lim  sum_{k >= 6} max(0, x_k - x_max,k + eta_lim)^2 + max(0, x_min,k + eta_lim - x_k)^2. */
 typedef struct bodex_energy_params {
   float w_q;
   float w_d;
   float delta;
   int kind;  /* BODEX_ENERGY_QP or BODEX_ENERGY_DFC */
+  float w_pen, w_self, w_lim;
+  float eta_pen;  /* activation distance of the penetration hinge (m), >= 0 */
+  float eta_lim;  /* margin inside the joint limits (rad), >= 0 */
 } bodex_energy_params;
 
 /* Upper-level step: Adam (lr_t for the 3 translations, lr_r for all

@@ -67,15 +67,19 @@ def step_params(params: dict | None = None, qp: _b.bodex_qp_params | None = None
                 grasps_per_cta: int = 0) -> _b.bodex_step_params:
     """Upper-level parameters (struct bodex_step_params) from a dict with keys
     lr_t, lr_r, b1, b2, adam_eps, w_q, w_d, delta, energy (ENERGY_QP or
-    ENERGY_DFC; and mu, beta, gamma, eps_reg used when `qp` is not given)."""
+    ENERGY_DFC), the collision energies w_pen, w_self, w_lim, eta_pen, eta_lim
+    (off at weight 0), and mu, beta, gamma, eps_reg used when `qp` is not
+    given."""
     p = dict(lr_t=2e-3, lr_r=2e-2, b1=0.9, b2=0.999, adam_eps=1e-8, w_q=1.0, w_d=1000.0, delta=0.01,
-             mu=0.5, beta=1.0, gamma=0.5, eps_reg=0.0, energy=_b.ENERGY_QP)
+             mu=0.5, beta=1.0, gamma=0.5, eps_reg=0.0, energy=_b.ENERGY_QP, w_pen=0.0, w_self=0.0, w_lim=0.0,
+             eta_pen=0.005, eta_lim=0.0)
     if params:
         p.update({k: v for k, v in params.items() if k in p})
     if qp is None:
         qp = qp_params(mu=p["mu"], beta=p["beta"], gamma=p["gamma"], eps_reg=p["eps_reg"])
     return _b.bodex_step_params(p["lr_t"], p["lr_r"], p["b1"], p["b2"], p["adam_eps"],
-                                _b.bodex_energy_params(p["w_q"], p["w_d"], p["delta"], int(p["energy"])), qp,
+                                _b.bodex_energy_params(p["w_q"], p["w_d"], p["delta"], int(p["energy"]), p["w_pen"],
+                                                       p["w_self"], p["w_lim"], p["eta_pen"], p["eta_lim"]), qp,
                                 int(grasps_per_cta))
 
 
@@ -95,11 +99,18 @@ class Hand:
         tips = getattr(tpl, "tip_samples", None)
         S = 0 if tips is None else int(tips.shape[1])
         keep["tips"] = _np(tips, np.float32) if tips is not None else None
+        sl = getattr(tpl, "sphere_link", None)
+        K = 0 if sl is None else int(len(sl))
+        keep["sl"] = _np(sl, np.int32) if K else None
+        keep["sp"] = _np(tpl.sphere_local, np.float32) if K else None
+        keep["sr"] = _np(tpl.sphere_radius, np.float32) if K else None
         fp = lambda a: a.ctypes.data_as(_b.c_float_p) if a is not None else None
-        ip = lambda a: a.ctypes.data_as(_b.c_int_p)
+        ip = lambda a: a.ctypes.data_as(_b.c_int_p) if a is not None else None
         desc = _b.bodex_hand_desc(self.n, self.m, ip(keep["parent"]), fp(keep["offset"]), fp(keep["axis"]),
                                   fp(keep["qmin"]), fp(keep["qmax"]), ip(keep["clink"]), fp(keep["clocal"]),
-                                  float(tpl.contact_radius), S, fp(keep["tips"]))
+                                  float(tpl.contact_radius), S, fp(keep["tips"]), K, ip(keep["sl"]),
+                                  fp(keep["sp"]), fp(keep["sr"]))
+        self.K = K
         h = C.c_void_p()
         _b.check(L.bodex_hand_create(C.byref(desc), C.byref(h)))
         self._h = h

@@ -41,7 +41,8 @@ class bodex_hand_desc(C.Structure):
     _fields_ = [("n_joints", C.c_int), ("n_contacts", C.c_int), ("parent", c_int_p), ("offset", c_float_p),
                 ("axis", c_float_p), ("qmin", c_float_p), ("qmax", c_float_p), ("contact_link", c_int_p),
                 ("contact_local", c_float_p), ("contact_radius", C.c_float), ("n_tip_samples", C.c_int),
-                ("tip_samples", c_float_p)]
+                ("tip_samples", c_float_p), ("n_spheres", C.c_int), ("sphere_link", c_int_p),
+                ("sphere_local", c_float_p), ("sphere_radius", c_float_p)]
 
 
 class bodex_object_desc(C.Structure):
@@ -56,7 +57,9 @@ class bodex_qp_params(C.Structure):
 
 
 class bodex_energy_params(C.Structure):
-    _fields_ = [("w_q", C.c_float), ("w_d", C.c_float), ("delta", C.c_float), ("kind", C.c_int)]
+    _fields_ = [("w_q", C.c_float), ("w_d", C.c_float), ("delta", C.c_float), ("kind", C.c_int),
+                ("w_pen", C.c_float), ("w_self", C.c_float), ("w_lim", C.c_float), ("eta_pen", C.c_float),
+                ("eta_lim", C.c_float)]
 
 
 class bodex_step_params(C.Structure):

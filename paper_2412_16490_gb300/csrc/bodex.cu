@@ -51,6 +51,8 @@ struct bodex_hand_s {
   HandDev host;
   HandDev* dev = nullptr;
   float* tips = nullptr;  // [m, S, 3] fingertip surface samples (refinement)
+  void* coll_mem = nullptr;  // collision spheres (one allocation behind coll's pointers)
+  CollDev coll{};
 };
 struct bodex_object_s {
   ObjDev dev;
@@ -94,7 +96,12 @@ struct Lay {
   static constexpr int oAM = oX + MAXD;
   static constexpr int oAV = oAM + MAXD;
   static constexpr int oJW = oAV + MAXD;  // chain joint axes/points, M x MAXCHAIN x 6
-  static constexpr int oSC = oJW + M * MAXCHAIN * 6;
+  static constexpr int oGC = oJW + M * MAXCHAIN * 6;  // collision gradient [MAXD], energy by lane [SMAX]
+  static constexpr int oSC = oGC + MAXD + SMAX;
+  // collision scratch: link frames in the K^-1 setup scratch, sphere centres
+  // and slot sums in the r / Q / dE/dG block (both dead before A4)
+  static constexpr int COLL_FR = WoodburyScratch<M, double>::floats;
+  static constexpr int COLL_CS = SMAX * (6 + NV) + SMAX + 6 * NV;
   // per-grasp stride == 12 (mod 32) words: the two or three grasps that
   // share a warp then map the same offset to different banks
   static constexpr int PER = align4(oSC + 4) + ((12 - align4(oSC + 4) % 32) + 32) % 32;
@@ -301,6 +308,9 @@ struct FusedArgs {
   float* res;        // [B] max ADMM residual of the grasp's QPs at the last step (may be null)
   int gpb;           // grasps per CTA
   int dfc;           // 1: the DFC force-closure energy |G u|^2 replaces the QPs (uniform per launch)
+  int coll;          // 1: the collision energies are on (uniform per launch)
+  CollDev cd;
+  CollParams cp;
 };
 
 // MODE_EVAL: E and dE/dx at x.  MODE_STEP: n_steps upper iterations on the
@@ -376,7 +386,8 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
     // ---- A1-A3: kinematics, nearest-point query, grasp matrix (lane = contact)
     if (active && lane < M) {
       float c[3];
-      fk_contact(H, lane, xs, c, per + L::oJW + lane * MAXCHAIN * 6);
+      fk_contact(H, lane, xs, c, per + L::oJW + lane * MAXCHAIN * 6,
+                 (A.coll && A.cd.K > 0) ? per + L::oK : nullptr);  // link frames for the collision spheres
       const ContactGeo k = contact_geometry(A.obj, c);
       store_ct(per + L::oCT + L::CTW * lane, k);
       write_G_block(k, lane, NV, Gs);
@@ -386,6 +397,11 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
       if (st) atomicOr(stat, st);
     }
     __syncthreads();
+    // ---- constraint energies on the collision spheres (Sec. IV-B)
+    if (A.coll)
+      collision_phase(active, lane, S, H, A.cd, A.obj, xs, A.cp, per + L::oK, per + L::oJW, per + L::oRY,
+                      per + L::oRY + 3 * A.cd.K, per + L::oRY + 3 * A.cd.K + 6 * (H.n + 1), per + L::oGC,
+                      per + L::oGC + MAXD);
     // ---- A4: K^-1 per grasp
     if (MODE != MODE_ADJOINT && !A.dfc) setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg);
     // ---- A5: ADMM, one QP per lane
@@ -461,7 +477,10 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
           const float r = per[L::oCT + L::CTW * i + 9] - H.alpha - A.delta;
           Ed = fmaf(r, r, Ed);
         }
-        sc[0] = A.w_q * EQ + A.w_d * Ed;
+        float Ec = 0.f;
+        if (A.coll)
+          for (int l = 0; l < S; ++l) Ec += per[L::oGC + MAXD + l];
+        sc[0] = A.w_q * EQ + A.w_d * Ed + Ec;
       }
     }
     if (active && !A.dfc) {
@@ -487,7 +506,10 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
           const float r = per[L::oCT + L::CTW * i + 9] - H.alpha - A.delta;
           Ed = fmaf(r, r, Ed);
         }
-        sc[0] = A.w_q * EQ + A.w_d * Ed;
+        float Ec = 0.f;
+        if (A.coll)
+          for (int l = 0; l < S; ++l) Ec += per[L::oGC + MAXD + l];
+        sc[0] = A.w_q * EQ + A.w_d * Ed + Ec;
       }
     }
     __syncthreads();
@@ -542,6 +564,7 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
             if (pos >= 0) g += cb[i * (6 + MAXCHAIN) + 6 + pos];
           }
         }
+        if (A.coll) g += per[L::oGC + k];
         if (MODE != MODE_STEP) {
           if (A.dEdx) A.dEdx[(size_t)b * D + k] = g;
         } else {
@@ -974,6 +997,130 @@ int run_metrics(const MetricsArgs& A, cudaStream_t st) {
 }
 }  // namespace
 
+// ============================================================================ hand collision spheres
+// Shared-memory room the fused kernel has for the collision scratch of one
+// grasp (sphere centres and per-slot sums), by contact count.
+static int coll_room(int m) {
+  switch (m) {
+    case 3: return Lay<3>::COLL_CS;
+    case 4: return Lay<4>::COLL_CS;
+    default: return Lay<5>::COLL_CS;
+  }
+}
+static int frame_room(int m) {
+  switch (m) {
+    case 3: return Lay<3>::COLL_FR;
+    case 4: return Lay<4>::COLL_FR;
+    default: return Lay<5>::COLL_FR;
+  }
+}
+
+// Orders the spheres by slot (link, then the root), bounds each slot's
+// spheres, lists the slot pairs allowed for self-penetration, and uploads
+// them in one allocation.  Pair rule: spheres on different links, except a
+// link and its nearest ancestor link that carries spheres (the root counts).
+static int upload_spheres(bodex_hand_s* h, const bodex_hand_desc* d) {
+  const int K = d->n_spheres, n = h->host.n;
+  if (K == 0) return BODEX_OK;
+  if (K < 0 || K > BODEX_MAX_SPHERES) return fail(BODEX_ERR_INVALID, "n_spheres out of range");
+  if (!d->sphere_link || !d->sphere_local || !d->sphere_radius)
+    return fail(BODEX_ERR_INVALID, "null sphere array in hand descriptor");
+  std::vector<int> slot(K);
+  for (int k = 0; k < K; ++k) {
+    const int L = d->sphere_link[k];
+    if (L < -1 || L >= n) return fail(BODEX_ERR_INVALID, "sphere_link out of range");
+    if (!(d->sphere_radius[k] > 0.f)) return fail(BODEX_ERR_INVALID, "sphere_radius must be > 0");
+    slot[k] = L < 0 ? n : L;
+  }
+
+  if (3 * K + 9 * (n + 1) > coll_room(h->host.m) || 12 * (n + 1) > frame_room(h->host.m))
+    return fail(BODEX_ERR_INVALID, "too many collision spheres and joints for this contact count");
+  // the collision phase takes its link frames from the contact kinematics
+  for (int k = 0; k < K; ++k) {
+    const int L = d->sphere_link[k];
+    bool on_chain = L < 0;
+    for (int i = 0; i < h->host.m && !on_chain; ++i) on_chain = h->host.jpos[i][L] >= 0;
+    if (!on_chain) return fail(BODEX_ERR_INVALID, "a sphere link lies on no contact chain");
+  }
+  std::vector<int> order(K);
+  for (int k = 0; k < K; ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return slot[a] < slot[b]; });
+  std::vector<char> has(n, 0);
+  for (int k = 0; k < K; ++k)
+    if (d->sphere_link[k] >= 0) has[d->sphere_link[k]] = 1;
+  auto eff_parent = [&](int L) {  // -1: the root; -2: none (L is the root)
+    if (L < 0) return -2;
+    int p = h->host.parent[L];
+    while (p >= 0 && !has[p]) p = h->host.parent[p];
+    return p;
+  };
+  std::vector<float4> sph(K);
+  std::vector<int> slot_start(n + 2, 0);
+  for (int a = 0; a < K; ++a) {
+    const int ka = order[a];
+    sph[a] = make_float4(d->sphere_local[3 * ka], d->sphere_local[3 * ka + 1], d->sphere_local[3 * ka + 2],
+                         d->sphere_radius[ka]);
+    ++slot_start[slot[ka] + 1];
+  }
+  for (int L = 0; L <= n; ++L) slot_start[L + 1] += slot_start[L];
+  // bounding sphere of each slot's spheres (centre: their mean), and the
+  // slot pairs allowed for self-penetration
+  std::vector<float4> sbound(n + 1, make_float4(0.f, 0.f, 0.f, 0.f));
+  for (int L = 0; L <= n; ++L) {
+    const int k0 = slot_start[L], k1 = slot_start[L + 1];
+    if (k0 == k1) continue;
+    double c[3] = {0, 0, 0};
+    for (int k = k0; k < k1; ++k) {
+      c[0] += sph[k].x;
+      c[1] += sph[k].y;
+      c[2] += sph[k].z;
+    }
+    for (double& v : c) v /= (k1 - k0);
+    double R = 0;
+    for (int k = k0; k < k1; ++k) {
+      const double dx = sph[k].x - c[0], dy = sph[k].y - c[1], dz = sph[k].z - c[2];
+      R = std::max(R, std::sqrt(dx * dx + dy * dy + dz * dz) + sph[k].w);
+    }
+    sbound[L] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)(R * (1.0 + 1e-5)) + 1e-6f);
+  }
+  auto link_of = [&](int L) { return L == n ? -1 : L; };
+  std::vector<int> spstart(n + 2, 0), spartners;
+  for (int L = 0; L <= n; ++L) {
+    for (int L2 = 0; L2 <= n; ++L2) {
+      if (L2 == L || slot_start[L] == slot_start[L + 1] || slot_start[L2] == slot_start[L2 + 1]) continue;
+      const int la = link_of(L), lb = link_of(L2);
+      if (eff_parent(la) == lb || eff_parent(lb) == la) continue;
+      spartners.push_back(L2);
+    }
+    spstart[L + 1] = (int)spartners.size();
+  }
+  const size_t b_sph = sizeof(float4) * K, b_sb = sizeof(float4) * (n + 1), b_ss = sizeof(int) * (n + 2),
+               b_sp = sizeof(int) * (n + 2), b_pa = sizeof(int) * std::max<size_t>(1, spartners.size());
+  const size_t o_sb = b_sph, o_ss = o_sb + b_sb, o_sp = o_ss + b_ss, o_pa = o_sp + b_sp;
+  std::vector<char> blob(o_pa + b_pa);
+  std::memcpy(blob.data(), sph.data(), b_sph);
+  std::memcpy(blob.data() + o_sb, sbound.data(), b_sb);
+  std::memcpy(blob.data() + o_ss, slot_start.data(), b_ss);
+  std::memcpy(blob.data() + o_sp, spstart.data(), b_sp);
+  if (!spartners.empty()) std::memcpy(blob.data() + o_pa, spartners.data(), sizeof(int) * spartners.size());
+  if (cudaMalloc(&h->coll_mem, blob.size()) != cudaSuccess) {
+    h->coll_mem = nullptr;
+    return fail(BODEX_ERR_OOM, "cudaMalloc collision spheres");
+  }
+  cudaError_t e = cudaMemcpy(h->coll_mem, blob.data(), blob.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy collision spheres");
+  char* base = static_cast<char*>(h->coll_mem);
+  h->coll.K = K;
+  h->coll.sph = reinterpret_cast<const float4*>(base);
+  h->coll.sbound = reinterpret_cast<const float4*>(base + o_sb);
+  h->coll.slot_start = reinterpret_cast<const int*>(base + o_ss);
+  h->coll.spstart = reinterpret_cast<const int*>(base + o_sp);
+  h->coll.spartners = reinterpret_cast<const int*>(base + o_pa);
+  return BODEX_OK;
+}
+
+extern "C" int bodex_hand_destroy(bodex_hand_t h);
+
 // ============================================================================ C ABI
 extern "C" {
 
@@ -1052,9 +1199,14 @@ int bodex_hand_create(const bodex_hand_desc* d, bodex_hand_t* out) {
   }
   e = cudaMemcpy(h->dev, &h->host, sizeof(HandDev), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
+    if (h->tips) cudaFree(h->tips);
     cudaFree(h->dev);
     delete h;
     return cuda_fail(e, "cudaMemcpy hand");
+  }
+  if (int r = upload_spheres(h, d)) {
+    bodex_hand_destroy(h);
+    return r;
   }
   *out = h;
   return BODEX_OK;
@@ -1063,6 +1215,7 @@ int bodex_hand_create(const bodex_hand_desc* d, bodex_hand_t* out) {
 int bodex_hand_destroy(bodex_hand_t h) {
   if (!h) return BODEX_OK;
   if (h->tips) cudaFree(h->tips);
+  if (h->coll_mem) cudaFree(h->coll_mem);
   cudaFree(h->dev);
   delete h;
   return BODEX_OK;
@@ -1296,6 +1449,11 @@ static int fill_args(FusedArgs& A, bodex_hand_t h, bodex_object_t o, const float
   if (p->energy.kind != BODEX_ENERGY_QP && p->energy.kind != BODEX_ENERGY_DFC)
     return fail(BODEX_ERR_INVALID, "energy.kind must be BODEX_ENERGY_QP or BODEX_ENERGY_DFC");
   A.dfc = p->energy.kind == BODEX_ENERGY_DFC;
+  const bodex_energy_params& e = p->energy;
+  if (!(e.eta_pen >= 0.f) || !(e.eta_lim >= 0.f)) return fail(BODEX_ERR_INVALID, "eta_pen and eta_lim must be >= 0");
+  A.coll = (e.w_pen != 0.f || e.w_self != 0.f || e.w_lim != 0.f) ? 1 : 0;
+  A.cd = h->coll;
+  A.cp = CollParams{e.w_pen, e.w_self, e.w_lim, e.eta_pen, e.eta_lim};
   return BODEX_OK;
 }
 

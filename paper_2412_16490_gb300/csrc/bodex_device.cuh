@@ -44,6 +44,25 @@ struct HandDev {
   int8_t jpos[MAXM][MAXJ];    // position of joint j in contact i's chain, or -1
 };
 
+// Collision spheres of a hand (device arrays, read through the read-only
+// cache).  Spheres are ordered by slot: slot L < n is link L, slot n the
+// root; slot L holds spheres slot_start[L] .. slot_start[L+1]-1 and has a
+// bounding sphere sbound[L] (in its frame) around them.  The slots whose
+// spheres pair with slot L's for self-penetration are
+// spartners[spstart[L] .. spstart[L+1]-1] (each slot pair appears under both).
+struct CollDev {
+  int K;
+  const float4* sph;     // [K] centre in the link frame (xyz), radius (w)
+  const float4* sbound;  // [n+1] bounding sphere of the slot's spheres
+  const int* slot_start;
+  const int* spstart;
+  const int* spartners;
+};
+
+struct CollParams {
+  float w_pen, w_self, w_lim, eta_pen, eta_lim;
+};
+
 struct ObjDev {
   int kind;  // 0 sphere, 1 grid
   float cx, cy, cz, r;
@@ -139,13 +158,22 @@ __device__ __forceinline__ void root_frame(const float* x, Tf& T, float om[3][3]
   om[2][0] = s2;  om[2][1] = -s1 * c2; om[2][2] = c1 * c2;
 }
 
+__device__ __forceinline__ void store_frame(const Tf& T, float* f) {
+#pragma unroll
+  for (int e = 0; e < 9; ++e) f[e] = T.R[e];
+  f[9] = T.t[0];
+  f[10] = T.t[1];
+  f[11] = T.t[2];
+}
+
 // Forward kinematics of contact i's link (Sec. IV-B): walks the chain from
 // the root and returns the link frame T; if `jw` is given, stores the world
 // axis and a point on the axis of every chain joint (6 floats each, in chain
 // order) for the adjoint.
-__device__ inline void fk_link(const HandDev& H, int i, const float* x, Tf& T, float* jw) {
+__device__ inline void fk_link(const HandDev& H, int i, const float* x, Tf& T, float* jw, float* frames = nullptr) {
   float om[3][3];
   root_frame(x, T, om);
+  if (frames) store_frame(T, frames + 12 * H.n);  // the root
   const int L = H.chain_len[i];
   for (int k = 0; k < L; ++k) {
     const int j = H.chain[i][k];
@@ -169,6 +197,7 @@ __device__ inline void fk_link(const HandDev& H, int i, const float* x, Tf& T, f
     rodrigues(a, x[6 + j], rq.R);
     rq.t[0] = rq.t[1] = rq.t[2] = 0.f;
     tf_mul(base, rq, T);
+    if (frames) store_frame(T, frames + 12 * j);
   }
 }
 
@@ -178,10 +207,13 @@ __device__ __forceinline__ void tf_point(const Tf& T, const float* p, float* c) 
   c[2] = fmaf(T.R[6], p[0], fmaf(T.R[7], p[1], fmaf(T.R[8], p[2], T.t[2])));
 }
 
-// Contact point c_{i,w} = R c_{i,l} + T of contact i (and chain frames, see fk_link).
-__device__ inline void fk_contact(const HandDev& H, int i, const float* x, float* c, float* jw) {
+// Contact point c_{i,w} = R c_{i,l} + T of contact i (and chain frames, see
+// fk_link; `frames`, if given, receives the frame of every chain link at
+// 12 j and the root frame at 12 n, row-major [R | t]).
+__device__ inline void fk_contact(const HandDev& H, int i, const float* x, float* c, float* jw,
+                                  float* frames = nullptr) {
   Tf T;
-  fk_link(H, i, x, T, jw);
+  fk_link(H, i, x, T, jw, frames);
   const float* cl = H.clocal[i];
   c[0] = fmaf(T.R[0], cl[0], fmaf(T.R[1], cl[1], fmaf(T.R[2], cl[2], T.t[0])));
   c[1] = fmaf(T.R[3], cl[0], fmaf(T.R[4], cl[1], fmaf(T.R[5], cl[2], T.t[1])));
@@ -798,6 +830,202 @@ __device__ inline void contact_adjoint(const ContactGeo& k, const float* dEdG_co
     }
     dEdc[cc] = fmaf(dist_coef, k.g[cc], s);
   }
+}
+
+// ------------------------------------------------------------------ collision energies
+// The constraint energies of Sec. IV-B (joint limits, Eq. (4); no hand-hand /
+// hand-object collision) on the hand's collision spheres, cuRobo style:
+//   E_pen  = w_pen  sum_k h(r_k + eta_pen - phi(c_k))   (quadratic-then-linear hinge)
+//   E_self = w_self sum_pairs max(0, r_a + r_b - |c_a - c_b|)^2
+//   E_lim  = w_lim  sum_{k >= 6} max(0, x_k - x_max,k + eta_lim)^2 + max(0, x_min,k + eta_lim - x_k)^2
+// and their gradient through the kinematic tree.  The gradient of joint j
+// collects, over the links L that joint j moves, the force sum F_L and the
+// moment sum tau_L = sum_k c_k x f_k of the sphere gradients f_k = dE/dc_k:
+//   dE/dq_j = w_j . (tau - o_j x F),  w_j, o_j: joint j's world axis and point.
+
+__device__ __forceinline__ float penetration_hinge(float p, float eta, float& dh) {
+  if (p <= 0.f) {
+    dh = 0.f;
+    return 0.f;
+  }
+  if (eta > 0.f && p <= eta) {
+    dh = p / eta;
+    return 0.5f * p * p / eta;
+  }
+  dh = 1.f;
+  return p - 0.5f * eta;
+}
+
+// One grasp's collision energies.  Lanes own slots (links, then the root)
+// and joints with stride S.  In (shared memory): frames [12 (n+1)] the link
+// and root frames and jw [m][MAXCHAIN][6] the chain joints' world axes and
+// points, both from the contact kinematics of this step (every link that
+// carries spheres lies on a contact chain).  Scratch: cs [3 K] sphere
+// centres; sl [6 (n+1)] per-slot (F, tau), turned into subtree sums in
+// place; bw [3 (n+1)] slot bounding-sphere centres.  Out: gc [D] the
+// gradient, ep [S] the energy by lane.  Must be called by every thread of
+// the CTA (contains barriers).
+// The argument structs are copied into registers first: through references
+// every use would be a local-memory load that stores to shared memory force
+// the compiler to repeat.
+__device__ __noinline__ void collision_phase(bool active, int lane, int S, const HandDev& H, const CollDev& Cr,
+                                             const ObjDev& Or, const float* x, const CollParams& Pr,
+                                             const float* frames, const float* jw, float* cs, float* sl, float* bw,
+                                             float* gc, float* ep) {
+  const CollDev C = Cr;
+  const ObjDev O = Or;
+  const CollParams P = Pr;
+  const int n = H.n, D = H.D, nslot = n + 1;
+  // a hand without spheres has no sphere tables (null pointers): only the
+  // joint-limit term applies.  C.K is uniform, so every thread still meets
+  // every barrier below.
+  const bool sph = C.K > 0;
+  float e = 0.f;
+  // C1: sphere centres from the slot frames
+  if (active && sph)
+    for (int L = lane; L < nslot; L += S) {
+      Tf T;
+#pragma unroll
+      for (int e2 = 0; e2 < 9; ++e2) T.R[e2] = frames[12 * L + e2];
+      T.t[0] = frames[12 * L + 9];
+      T.t[1] = frames[12 * L + 10];
+      T.t[2] = frames[12 * L + 11];
+      const int k1 = __ldg(C.slot_start + L + 1);
+      for (int k = __ldg(C.slot_start + L); k < k1; ++k) {
+        const float4 sp = __ldg(C.sph + k);
+        const float p[3] = {sp.x, sp.y, sp.z};
+        tf_point(T, p, cs + 3 * k);
+      }
+      const float4 sb = __ldg(C.sbound + L);
+      const float pb[3] = {sb.x, sb.y, sb.z};
+      tf_point(T, pb, bw + 3 * L);
+    }
+  __syncthreads();
+  // C2: sphere gradients f_k, summed per slot into (F, tau).  Self pairs:
+  // only between slots whose bounding spheres overlap (a mask per slot).
+  if (active && sph)
+    for (int L = lane; L < nslot; L += S) {
+      unsigned long long near = 0ull;
+      if (P.w_self != 0.f) {
+        const float4 bL = __ldg(C.sbound + L);
+        const float cL[3] = {bw[3 * L], bw[3 * L + 1], bw[3 * L + 2]};
+        const int q1 = __ldg(C.spstart + L + 1);
+        for (int q = __ldg(C.spstart + L); q < q1; ++q) {
+          const int L2 = __ldg(C.spartners + q);
+          const float dx = cL[0] - bw[3 * L2], dy = cL[1] - bw[3 * L2 + 1], dz = cL[2] - bw[3 * L2 + 2];
+          const float rr = bL.w + __ldg(C.sbound + L2).w;
+          if (dx * dx + dy * dy + dz * dz < rr * rr) near |= 1ull << L2;
+        }
+      }
+      float F[3] = {0.f, 0.f, 0.f}, tau[3] = {0.f, 0.f, 0.f};
+      const int k1 = __ldg(C.slot_start + L + 1);
+      for (int k = __ldg(C.slot_start + L); k < k1; ++k) {
+        const float c[3] = {cs[3 * k], cs[3 * k + 1], cs[3 * k + 2]};
+        const float r = __ldg(C.sph + k).w;
+        float f[3] = {0.f, 0.f, 0.f};
+        if (P.w_pen != 0.f) {
+          const SdfQ q = sdf_query(O, c);
+          float dh;
+          e = fmaf(P.w_pen, penetration_hinge(r + P.eta_pen - q.phi, P.eta_pen, dh), e);
+          const float sc = -P.w_pen * dh;
+#pragma unroll
+          for (int a = 0; a < 3; ++a) f[a] = sc * q.g[a];
+        }
+        for (unsigned long long m2 = near; m2; m2 &= m2 - 1ull) {
+          const int L2 = __ffsll((long long)m2) - 1;
+          const int t1 = __ldg(C.slot_start + L2 + 1);
+          for (int o = __ldg(C.slot_start + L2); o < t1; ++o) {
+            const float v[3] = {c[0] - cs[3 * o], c[1] - cs[3 * o + 1], c[2] - cs[3 * o + 2]};
+            const float len2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2];
+            const float rr = r + __ldg(C.sph + o).w;
+            if (len2 < rr * rr) {
+              const float len = sqrtf(len2);
+              const float d = rr - len;
+              e = fmaf(0.5f * P.w_self * d, d, e);  // each pair is visited from both spheres
+              const float sc = -2.f * P.w_self * d / len;
+#pragma unroll
+              for (int a = 0; a < 3; ++a) f[a] = fmaf(sc, v[a], f[a]);
+            }
+          }
+        }
+        float cf[3];
+        cross3(c, f, cf);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+          F[a] += f[a];
+          tau[a] += cf[a];
+        }
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        sl[6 * L + a] = F[a];
+        sl[6 * L + 3 + a] = tau[a];
+      }
+    }
+  __syncthreads();
+  // C3a: subtree sums, leaves first (parent[j] < j), by one lane; slot n
+  // (the root) becomes the total
+  if (active && sph && lane == 0)
+    for (int j = n - 1; j >= 0; --j) {
+      const int p = H.parent[j];
+      const int to = p < 0 ? n : p;
+#pragma unroll
+      for (int a = 0; a < 6; ++a) sl[6 * to + a] += sl[6 * j + a];
+    }
+  __syncthreads();
+  // C3b: joint gradients dE/dq_j = w_j . (tau_sub - o_j x F_sub) over the
+  // links joint j moves (the root joints: everything), and the limit energy
+  if (active) {
+    for (int k = lane; k < D; k += S) {
+      float g = 0.f;
+      if (sph) {
+        const float* sub = sl + 6 * (k < 6 ? n : k - 6);
+        if (k < 3) {
+          g = sub[k];
+        } else {
+          float w[3], o[3];
+          if (k < 6) {
+            Tf T;
+            float om[3][3];
+            root_frame(x, T, om);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              w[a] = om[k - 3][a];
+              o[a] = x[a];
+            }
+          } else {
+            // joint k-6 on some contact chain (else its subtree has no spheres)
+            const float* ax = nullptr;
+            for (int i = 0; i < H.m && !ax; ++i)
+              if (H.jpos[i][k - 6] >= 0) ax = jw + (i * MAXCHAIN + H.jpos[i][k - 6]) * 6;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              w[a] = ax ? ax[a] : 0.f;
+              o[a] = ax ? ax[3 + a] : 0.f;
+            }
+          }
+          const float Fs[3] = {sub[0], sub[1], sub[2]};
+          float oF[3];
+          cross3(o, Fs, oF);
+          g = w[0] * (sub[3] - oF[0]) + w[1] * (sub[4] - oF[1]) + w[2] * (sub[5] - oF[2]);
+        }
+      }
+      if (k >= 6 && P.w_lim != 0.f) {
+        const float hi = x[k] - H.qmax[k] + P.eta_lim, lo = H.qmin[k] + P.eta_lim - x[k];
+        if (hi > 0.f) {
+          e = fmaf(P.w_lim * hi, hi, e);
+          g = fmaf(2.f * P.w_lim, hi, g);
+        }
+        if (lo > 0.f) {
+          e = fmaf(P.w_lim * lo, lo, e);
+          g = fmaf(-2.f * P.w_lim, lo, g);
+        }
+      }
+      gc[k] = g;
+    }
+    ep[lane] = e;
+  }
+  __syncthreads();  // the scratch (fr, cs, sl) is reused by the next phase
 }
 
 }  // namespace bodex

@@ -89,6 +89,8 @@ def _sig(L):
     L.orc_refine_run.argtypes = [_v, _v, _d, _d, _d, C.c_int, _d, C.c_int, C.c_int, C.c_double, C.c_double,
                                  _d, C.c_int, _d]
     L.orc_contact_metrics.argtypes = [_v, _v, _d, C.c_int, C.c_int, _d, _d]
+    L.orc_qp_soc.argtypes = [_d, C.c_int, C.c_int, _d, C.c_int] + [C.c_double] * 4 + [C.c_int, C.c_int, _d, _d, _d,
+                                                                                        _d, _i, _d]
 
 
 def _p(a, t):
@@ -239,6 +241,26 @@ def qp_solve(G, T, mu=0.5, beta=1.0, gamma=0.5, eps_reg=0.0, threads=None, want_
     if want_lam:
         out["lam"] = lam
     return out
+
+
+def qp_soc(G, T, mu=0.5, beta=1.0, gamma=0.5, eps_reg=0.0, K=256, threads=None):
+    """Elliptic friction cone (the unlinearised contact model), bracketed by
+    exact QPs over the K-facet pyramids inscribed in and circumscribed about
+    the cone: Q_out <= Q* <= Q_in.  Returns dict y [B,s,3m] (the inscribed
+    optimum, feasible for the cone), Q_in, Q_out, kkt, status, lam
+    [B,s,4m+1] (rows: per contact f_n, the cone rows (mu f_n, f_d, f_e); then
+    the sum row)."""
+    G = _f64(G)
+    T = _f64(T)
+    B, nv = G.shape[0], G.shape[2]
+    m, s = nv // 3, T.shape[0]
+    y = np.zeros((B, s, nv))
+    Qi, Qo, kkt = np.zeros((B, s)), np.zeros((B, s)), np.zeros((B, s))
+    st = np.zeros((B, s), np.int32)
+    lam = np.zeros((B, s, 4 * m + 1))
+    _load().orc_qp_soc(_p(G, _d), B, m, _p(T, _d), s, mu, beta, gamma, eps_reg, int(K), threads or default_threads(),
+                       _p(y, _d), _p(Qi, _d), _p(Qo, _d), _p(kkt, _d), _p(st, _i), _p(lam, _d))
+    return dict(y=y, Q_in=Qi, Q_out=Qo, kkt=kkt, status=st, lam=lam)
 
 
 def qp_bruteforce(G, T, mu=0.5, beta=1.0, gamma=0.5, eps_reg=0.0, threads=None):

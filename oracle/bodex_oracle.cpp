@@ -437,14 +437,18 @@ struct QPProblem {
   double eps = 0;  // optional regulariser eps |y|^2
 };
 
-QPProblem make_qp(const double* G, int m, const double* t, double mu, double beta, double gamma,
-                  double eps_reg) {
+// Rows of the QP constraints A y >= b, per contact: f_n >= 0, -f_n >= -1,
+// then K facets mu_f f_n - cos(phi_k) f_d - sin(phi_k) f_e >= 0 with
+// phi_k = (2k+1) pi / K; the sum row sum f_n >= gamma last.  The pyramid of
+// Sec. IV-A is K = 8 with mu_f = mu cos(pi/8) (inscribed in the cone).
+QPProblem make_qp_facets(const double* G, int m, const double* t, double mu_f, int K, double beta, double gamma,
+                         double eps_reg) {
   QPProblem Pb;
   Pb.m = m;
   Pb.nv = 3 * m;
   Pb.eps = eps_reg;
-  const int nv = Pb.nv;
-  Pb.nin = 10 * m + 1;
+  const int nv = Pb.nv, R = 2 + K;
+  Pb.nin = R * m + 1;
   Pb.G.assign(G, G + 6 * nv);
   Pb.w.resize(6);
   for (int r = 0; r < 6; ++r) Pb.w[r] = beta * t[r];
@@ -465,27 +469,32 @@ QPProblem make_qp(const double* G, int m, const double* t, double mu, double bet
   Pb.A.assign((size_t)Pb.nin * nv, 0.0);
   Pb.b.assign(Pb.nin, 0.0);
   const double PI = 3.14159265358979323846;
-  const double mc = mu * std::cos(PI / 8);
   for (int i = 0; i < m; ++i) {
-    double* r0 = &Pb.A[(size_t)(10 * i) * nv];
+    double* r0 = &Pb.A[(size_t)(R * i) * nv];
     r0[3 * i] = 1.0;
-    Pb.b[10 * i] = 0.0;
-    double* r1 = &Pb.A[(size_t)(10 * i + 1) * nv];
+    Pb.b[R * i] = 0.0;
+    double* r1 = &Pb.A[(size_t)(R * i + 1) * nv];
     r1[3 * i] = -1.0;
-    Pb.b[10 * i + 1] = -1.0;
-    for (int k = 0; k < 8; ++k) {
-      const double ph = (2 * k + 1) * PI / 8;
-      double* rk = &Pb.A[(size_t)(10 * i + 2 + k) * nv];
-      rk[3 * i] = mc;
+    Pb.b[R * i + 1] = -1.0;
+    for (int k = 0; k < K; ++k) {
+      const double ph = (2 * k + 1) * PI / K;
+      double* rk = &Pb.A[(size_t)(R * i + 2 + k) * nv];
+      rk[3 * i] = mu_f;
       rk[3 * i + 1] = -std::cos(ph);
       rk[3 * i + 2] = -std::sin(ph);
-      Pb.b[10 * i + 2 + k] = 0.0;
+      Pb.b[R * i + 2 + k] = 0.0;
     }
   }
-  double* rs = &Pb.A[(size_t)(10 * m) * nv];
+  double* rs = &Pb.A[(size_t)(R * m) * nv];
   for (int i = 0; i < m; ++i) rs[3 * i] = 1.0;
-  Pb.b[10 * m] = gamma;
+  Pb.b[R * m] = gamma;
   return Pb;
+}
+
+QPProblem make_qp(const double* G, int m, const double* t, double mu, double beta, double gamma,
+                  double eps_reg) {
+  const double PI = 3.14159265358979323846;
+  return make_qp_facets(G, m, t, mu * std::cos(PI / 8), 8, beta, gamma, eps_reg);
 }
 
 double qp_value(const QPProblem& Pb, const double* y) {
@@ -649,7 +658,7 @@ QPResult qp_active_set(const QPProblem& Pb) {
   QPResult R;
   R.y.assign(nv, 0.0);
   R.lam.assign(nin, 0.0);
-  const double gamma = Pb.b[10 * m];
+  const double gamma = Pb.b[nin - 1];  // the sum row is last
   if (!(gamma <= m) || gamma < 0) {
     R.status = 2;
     return R;
@@ -969,6 +978,58 @@ struct Eval {
 // Distance-energy reading: the paper's coarse term is (|c - p| - alpha)^2
 // (Sec. IV-C); the signed SDF value replaces |c - p| so that penetration is
 // penalised, and delta is the pre-grasp margin (Sec. IV-D).
+// ---------------------------------------------------------------- elliptic friction cone
+// The unlinearised contact model (Sec. III, the paper's Eqs. before the
+// pyramid of Sec. IV-A): each force in the elliptic cone |(f_d, f_e)| <=
+// mu f_n with 0 <= f_n <= 1, plus sum f_n >= gamma -- a second-order-cone
+// program.  Its optimum Q* is bracketed by two exact polyhedral QPs: the
+// K-facet pyramid inscribed in the cone (facet distance mu cos(pi/K)) gives
+// Q_in >= Q* with a point y_in that is feasible for the cone, and the
+// circumscribed one (facet distance mu) gives Q_out <= Q*.  The bracket
+// closes as 1 - cos(pi/K).  Multipliers in the GPU's row form (per contact
+// the f_n row, then the cone rows (mu f_n, f_d, f_e); then the sum row)
+// come from the inscribed solve: the facets' combine into a point of the
+// polar cone.
+struct SocResult {
+  Vec y, lam;  // y = y_in; lam: 4m + 1 rows
+  double Q_in = 0, Q_out = 0, kkt = 0;
+  int status = 0;  // 0 ok, 1 an active-set solve hit its cap, 2 infeasible parameters
+};
+
+SocResult qp_soc(const double* G, int m, const double* t6, double mu, double beta, double gamma, double eps_reg,
+                 int K) {
+  const double PI = 3.14159265358979323846;
+  SocResult R;
+  QPProblem Pin = make_qp_facets(G, m, t6, mu * std::cos(PI / K), K, beta, gamma, eps_reg);
+  QPProblem Pout = make_qp_facets(G, m, t6, mu, K, beta, gamma, eps_reg);
+  QPResult Ri = qp_active_set(Pin), Ro = qp_active_set(Pout);
+  R.y = Ri.y;
+  R.Q_in = Ri.Q;
+  R.Q_out = Ro.Q;
+  R.kkt = std::max(Ri.kkt, Ro.kkt);
+  R.status = std::max(Ri.status, Ro.status);
+  R.lam.assign(4 * m + 1, 0.0);
+  const int rows = 2 + K;
+  const double mf = mu * std::cos(PI / K);
+  for (int i = 0; i < m; ++i) {
+    // A y >= b rows with multiplier l >= 0 enter grad f = sum l a; the row
+    // form has grad f + A_row^T lam = 0, so lam = -(the rows' combination)
+    R.lam[4 * i] = Ri.lam[rows * i + 1] - Ri.lam[rows * i];  // f_n <= 1 (upper) minus f_n >= 0 (lower)
+    double v0 = 0, v1 = 0, v2 = 0;
+    for (int k = 0; k < K; ++k) {
+      const double l = Ri.lam[rows * i + 2 + k], ph = (2 * k + 1) * PI / K;
+      v0 += l * mf / mu;
+      v1 -= l * std::cos(ph);
+      v2 -= l * std::sin(ph);
+    }
+    R.lam[4 * i + 1] = -v0;
+    R.lam[4 * i + 2] = -v1;
+    R.lam[4 * i + 3] = -v2;
+  }
+  R.lam[4 * m] = -Ri.lam[rows * m];
+  return R;
+}
+
 // ---------------------------------------------------------------- collision energies
 // The constraints of Eq. (4) (joint limits) and "no hand-hand / hand-object
 // collision", as cuRobo-style energies on the hand's collision spheres
@@ -1531,6 +1592,25 @@ void orc_qp_solve(const double* G, int B, int m, const double* T, int s, double 
     status[idx] = R.status;
     if (lam) std::copy(R.lam.begin(), R.lam.end(), lam + (size_t)idx * nin);
     if (iters) iters[idx] = R.iters;
+  });
+}
+
+// Elliptic-cone problems (qp_soc, K facets per bracketing pyramid) for B x s
+// wrenches: y [B,s,3m] (the inscribed optimum), Q_in, Q_out [B,s], kkt,
+// status [B,s], lam [B,s,4m+1] (may be NULL).
+void orc_qp_soc(const double* G, int B, int m, const double* T, int s, double mu, double beta, double gamma,
+                double eps_reg, int K, int threads, double* y, double* Q_in, double* Q_out, double* kkt,
+                int32_t* status, double* lam) {
+  const int nv = 3 * m;
+  parallel_for(B * s, threads, [&](int idx) {
+    const int b = idx / s, j = idx % s;
+    SocResult R = qp_soc(G + (size_t)b * 6 * nv, m, T + 6 * j, mu, beta, gamma, eps_reg, K);
+    std::copy(R.y.begin(), R.y.end(), y + (size_t)idx * nv);
+    Q_in[idx] = R.Q_in;
+    Q_out[idx] = R.Q_out;
+    kkt[idx] = R.kkt;
+    status[idx] = R.status;
+    if (lam) std::copy(R.lam.begin(), R.lam.end(), lam + (size_t)idx * (4 * m + 1));
   });
 }
 

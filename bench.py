@@ -268,6 +268,7 @@ def run_ours(args, rank, world, local_rank):
         extra["synthesis"] = synthesis_rate(bx, torch, H, Ob, x_dev, T_dev, sp)
         extra["energies"] = energy_variants(bx, torch, H, Ob, x_dev, T_dev, P)
         extra["qp_solves"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev)
+        extra["qp_solves_elliptic_cone"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev, cone=bx.CONE_ELLIPTIC)
         extra["e2e"] = e2e_rate(bx, torch, H, Ob, st, x0, T_dev, sp)
         extra["persistent_mixed"] = persistent_mixed(bx, torch, P)
         if args.serve_jobs > 0:
@@ -483,6 +484,7 @@ def synthesis_rate(bx, torch, H, Ob, x_dev, T_dev, sp, reps=2):
 def energy_variants(bx, torch, H, Ob, x_dev, T_dev, P, reps=3):
     """The comparison energies of Sec. V-C in the same fused 200-step run:
     DFC (no QP) and the QP baseline (beta = 0), next to the paper's energy;
+    the paper's energy on the elliptic friction cone instead of the pyramid;
     and the paper's energy with the collision-sphere constraint energies of
     Sec. IV-B (penetration, self-penetration, joint limits) switched on."""
     B = int(x_dev.shape[0])
@@ -492,6 +494,7 @@ def energy_variants(bx, torch, H, Ob, x_dev, T_dev, P, reps=3):
     for name, prm, qp in (("qp_beta1", dict(P), bx.qp_params(max_iter=ADMM_ITERS)),
                           ("qp_baseline_beta0", dict(P, beta=0.0), bx.qp_params(beta=0.0, max_iter=ADMM_ITERS)),
                           ("dfc", dict(P, energy=bx.ENERGY_DFC), bx.qp_params(max_iter=ADMM_ITERS)),
+                          ("qp_beta1_elliptic_cone", dict(P), bx.qp_params(max_iter=ADMM_ITERS, cone=bx.CONE_ELLIPTIC)),
                           ("qp_beta1_with_collision_energies",
                            dict(P, w_pen=100.0, w_self=100.0, w_lim=10.0, eta_pen=0.005, eta_lim=0.05),
                            bx.qp_params(max_iter=ADMM_ITERS))):
@@ -512,11 +515,12 @@ def energy_variants(bx, torch, H, Ob, x_dev, T_dev, P, reps=3):
     return out
 
 
-def qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev):
+def qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev, cone=0):
     """Standalone batched QPs at the paper-scale geometry: B*s = 49152 QPs,
-    cold start, iterate to 1e-5 (inf-norm primal and dual), cap 5000."""
+    cold start, iterate to 1e-5 (inf-norm primal and dual), cap 5000; the
+    8-facet pyramid or the elliptic cone."""
     G = bx.bodex_fk_contacts(H, Ob, x_dev)["G"]
-    prm = bx.qp_params(eps_abs=1e-5, max_iter=5000, check_every=10)
+    prm = bx.qp_params(eps_abs=1e-5, max_iter=5000, check_every=10, cone=cone)
     bx.bodex_qp_solve_batch(G, T_dev, prm)  # warm-up
     torch.cuda.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -161,7 +161,16 @@ typedef struct bodex_qp_params {
   int warm;          /* 1: start from the y/z/lam passed in, 0: from zero */
   int strict;        /* 1: return BODEX_ERR_NOT_CONVERGED if any QP missed eps_abs
                         (forces a stream synchronisation) */
+  int cone;          /* BODEX_CONE_PYRAMID: the 8-facet pyramid of Sec. IV-A (a QP);
+                        BODEX_CONE_ELLIPTIC: the unlinearised cone |(f_d, f_e)| <= mu f_n
+                        (a second-order-cone program, solved by ADMM with the cone's
+                        projection).  ADMM rows, for z and lam: per contact f_n, then
+                        8 facets (pyramid, 9m+1 rows in all) or the cone rows
+                        (mu f_n, f_d, f_e) (elliptic, 4m+1 rows in all); the sum row last. */
 } bodex_qp_params;
+
+#define BODEX_CONE_PYRAMID 0
+#define BODEX_CONE_ELLIPTIC 1
 
 /* Energy weights (Sec. IV-C): E = w_q sum_j Q_j + w_d sum_i (phi_i - alpha - delta)^2;
  * delta is the 1 cm pre-grasp margin of Sec. IV-D in the coarse stage. */

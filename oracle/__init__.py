@@ -26,10 +26,11 @@ _lib = None
 
 PARAM_KEYS = ("mu", "beta", "gamma", "w_q", "w_d", "delta", "eps_reg",
               "lr_t", "lr_r", "b1", "b2", "adam_eps", "energy",
-              "w_pen", "w_self", "w_lim", "eta_pen", "eta_lim")
+              "w_pen", "w_self", "w_lim", "eta_pen", "eta_lim", "cone", "cone_facets")
 ENERGY_QP, ENERGY_DFC = 0, 1
+CONE_PYRAMID, CONE_ELLIPTIC = 0, 1
 _PARAM_DEFAULTS = {"energy": ENERGY_QP, "w_pen": 0.0, "w_self": 0.0, "w_lim": 0.0, "eta_pen": 0.005,
-                   "eta_lim": 0.0}
+                   "eta_lim": 0.0, "cone": CONE_PYRAMID, "cone_facets": 512}
 
 
 def build(force: bool = False) -> str:

@@ -946,10 +946,12 @@ struct Params {
   double mu, beta, gamma, w_q, w_d, delta, eps_reg, lr_t, lr_r, b1, b2, adam_eps;
   int energy;
   double w_pen, w_self, w_lim, eta_pen, eta_lim;  // collision energies (collision_energy)
+  int cone;         // 0: the 8-facet pyramid; 1: the elliptic cone (qp_soc, inscribed bound)
+  int cone_facets;  // K of qp_soc
 };
 Params params_from(const double* a) {
   return {a[0], a[1], a[2], a[3], a[4], a[5], a[6], a[7], a[8], a[9], a[10], a[11], (int)a[12],
-          a[13], a[14], a[15], a[16], a[17]};
+          a[13], a[14], a[15], a[16], a[17], (int)a[18], (int)a[19]};
 }
 
 // DFC (Liu et al. 2021) assumes frictionless contacts that all push with the
@@ -1154,6 +1156,15 @@ Eval evaluate(const Hand& H, const Object& O, const double* x, const Params& P, 
     double w[6];
     dfc_wrench(ev.G, m, w);
     for (int r = 0; r < 6; ++r) EQ += w[r] * w[r];
+  } else if (P.cone == 1) {  // Q_j from the inscribed K-facet pyramid (within 1 - cos(pi/K) of the cone)
+    ev.qp.resize(s);
+    for (int j = 0; j < s; ++j) {
+      SocResult R = qp_soc(ev.G.data(), m, T + 6 * j, P.mu, P.beta, P.gamma, P.eps_reg, P.cone_facets);
+      ev.qp[j].y = R.y;
+      ev.qp[j].Q = R.Q_in;
+      ev.qp[j].status = R.status;
+      EQ += R.Q_in;
+    }
   } else {
     ev.qp.resize(s);
     for (int j = 0; j < s; ++j) {

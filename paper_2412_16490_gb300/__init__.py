@@ -14,7 +14,7 @@ import ctypes as C
 import numpy as np
 
 from . import _binding as _b
-from ._binding import BodexError, ENERGY_DFC, ENERGY_QP, ST_DEGENERATE_NORMAL, ST_NONFINITE, ST_NOT_CONVERGED  # noqa: F401
+from ._binding import BodexError, CONE_ELLIPTIC, CONE_PYRAMID, ENERGY_DFC, ENERGY_QP, ST_DEGENERATE_NORMAL, ST_NONFINITE, ST_NOT_CONVERGED  # noqa: F401
 
 __all__ = [
     "load", "Hand", "Object", "State", "qp_params", "step_params",
@@ -57,10 +57,10 @@ def _np(a, dt):
 
 # ---------------------------------------------------------------- parameters
 def qp_params(mu=0.5, beta=1.0, gamma=0.5, rho=0.1, sigma=1e-6, alpha=1.6, eps_abs=0.0, eps_reg=0.0,
-              max_iter=50, check_every=10, warm=0, strict=0) -> _b.bodex_qp_params:
-    """ADMM/QP parameters (struct bodex_qp_params)."""
+              max_iter=50, check_every=10, warm=0, strict=0, cone=0) -> _b.bodex_qp_params:
+    """ADMM/QP parameters (struct bodex_qp_params); cone: CONE_PYRAMID or CONE_ELLIPTIC."""
     return _b.bodex_qp_params(mu, beta, gamma, rho, sigma, alpha, eps_abs, eps_reg, int(max_iter),
-                              int(check_every), int(warm), int(strict))
+                              int(check_every), int(warm), int(strict), int(cone))
 
 
 def step_params(params: dict | None = None, qp: _b.bodex_qp_params | None = None,
@@ -236,7 +236,7 @@ def bodex_qp_solve_batch(G, T, params: _b.bodex_qp_params, y=None, z=None, lam=N
     torch = _torch()
     B, nv = int(G.shape[0]), int(G.shape[2])
     m, s = nv // 3, int(T.shape[0])
-    nc = 9 * m + 1
+    nc = 4 * m + 1 if params.cone == _b.CONE_ELLIPTIC else 9 * m + 1
     dev = G.device
     f = lambda *sh: torch.zeros(sh, dtype=torch.float32, device=dev)
     y = f(B, s, nv) if y is None else y

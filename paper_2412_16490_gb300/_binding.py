@@ -27,6 +27,7 @@ ST_DEGENERATE_NORMAL = 4
 
 # Every symbol include/bodex.h declares (checked by the CPU test-suite).
 ENERGY_QP, ENERGY_DFC = 0, 1
+CONE_PYRAMID, CONE_ELLIPTIC = 0, 1
 
 EXPORTS = (
     "bodex_hand_create", "bodex_hand_destroy", "bodex_object_create", "bodex_object_destroy",
@@ -53,7 +54,8 @@ class bodex_object_desc(C.Structure):
 class bodex_qp_params(C.Structure):
     _fields_ = [("mu", C.c_float), ("beta", C.c_float), ("gamma", C.c_float), ("rho", C.c_float),
                 ("sigma", C.c_float), ("alpha", C.c_float), ("eps_abs", C.c_float), ("eps_reg", C.c_float),
-                ("max_iter", C.c_int), ("check_every", C.c_int), ("warm", C.c_int), ("strict", C.c_int)]
+                ("max_iter", C.c_int), ("check_every", C.c_int), ("warm", C.c_int), ("strict", C.c_int),
+                ("cone", C.c_int)]
 
 
 class bodex_energy_params(C.Structure):

@@ -205,14 +205,14 @@ __device__ inline void setup_kinv(bool active, int lane, int S, const float* Gs,
 }
 
 // ============================================================================ kernel: batched QP
-template <int M>
+template <int M, int CONE>
 __global__ void __launch_bounds__(CTA_LANES) qp_solve_kernel(const float* __restrict__ Gin, int B,
                                                              const float* __restrict__ T, int S, AdmmCfg cfg,
                                                              int warm, float* yio, float* zio, float* lio,
                                                              float* Qout, int32_t* iters_out, int32_t* status_out,
                                                              float* res_out) {
   using L = Lay<M>;
-  constexpr int NV = L::NV, NC = L::NC;
+  constexpr int NV = L::NV, NC = CONE == CONE_SOC ? 4 * M + 1 : L::NC;  // ADMM rows
   extern __shared__ __align__(16) float smem[];
   const int GPB = blockDim.x / S;
   const int gl = threadIdx.x / S, lane = threadIdx.x % S;
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(CTA_LANES) qp_solve_kernel(const float* __rest
   }
   float rp, rd;
   bool conv;
-  const int it = admm_solve<M>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
+  const int it = admm_solve<M, CONE>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
   float Q = 0.f;
   bool fin = true;
 #pragma unroll
@@ -265,7 +265,7 @@ __global__ void __launch_bounds__(CTA_LANES) qp_solve_kernel(const float* __rest
   }
 #pragma unroll
   for (int r = 0; r < NC; ++r) {
-    const float p = proj_row<M>(w[r], r, cfg.gamma);
+    const float p = CONE == CONE_SOC ? proj_row_soc<M>(w, r, cfg.gamma) : proj_row<M>(w[r], r, cfg.gamma);
     zio[q * NC + r] = p;
     lio[q * NC + r] = cfg.rho * (w[r] - p);
   }
@@ -418,7 +418,8 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
         float mq[NV];
         neg_q<M>(Gs, t, cfg.beta, mq);
         float rp, rd;
-        admm_solve<M>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
+        if (cfg.cone) admm_solve<M, CONE_SOC>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
+        else admm_solve<M, CONE_PYR>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
         if (step == A.n_steps - 1) atomicMax(reinterpret_cast<int*>(sc + 2), __float_as_int(fmaxf(rp, rd)));
       }
       float* ry = per + L::oRY + lane * (6 + NV);
@@ -919,6 +920,8 @@ int check_qp_params(const bodex_qp_params* p, int m) {
   if (!(p->rho > 0.f) || !(p->sigma >= 0.f) || !(p->alpha > 0.f && p->alpha < 2.f) || p->max_iter < 0 ||
       !(p->mu >= 0.f))
     return fail(BODEX_ERR_INVALID, "invalid ADMM parameters");
+  if (p->cone != BODEX_CONE_PYRAMID && p->cone != BODEX_CONE_ELLIPTIC)
+    return fail(BODEX_ERR_INVALID, "cone must be BODEX_CONE_PYRAMID or BODEX_CONE_ELLIPTIC");
   return BODEX_OK;
 }
 
@@ -964,9 +967,15 @@ int run_qp(const float* G, int B, const float* T, int s, const AdmmCfg& cfg, int
   if (B == 0) return BODEX_OK;
   const int gpb = gpb_for<M>(s);
   const size_t bytes = Lay<M>::bytes(gpb);
-  if (int r = ensure_smem(qp_solve_kernel<M>, bytes)) return r;
-  qp_solve_kernel<M><<<(B + gpb - 1) / gpb, gpb * s, bytes, st>>>(G, B, T, s, cfg, warm, y, z, lam, Q, iters,
-                                                                  status, res);
+  if (cfg.cone) {
+    if (int r = ensure_smem(qp_solve_kernel<M, CONE_SOC>, bytes)) return r;
+    qp_solve_kernel<M, CONE_SOC><<<(B + gpb - 1) / gpb, gpb * s, bytes, st>>>(G, B, T, s, cfg, warm, y, z, lam, Q,
+                                                                              iters, status, res);
+  } else {
+    if (int r = ensure_smem(qp_solve_kernel<M, CONE_PYR>, bytes)) return r;
+    qp_solve_kernel<M, CONE_PYR><<<(B + gpb - 1) / gpb, gpb * s, bytes, st>>>(G, B, T, s, cfg, warm, y, z, lam, Q,
+                                                                              iters, status, res);
+  }
   return launch_err("qp_solve_kernel launch");
 }
 

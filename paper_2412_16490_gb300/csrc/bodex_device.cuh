@@ -12,10 +12,6 @@
 
 #include "../../include/bodex.h"
 
-#ifndef BODEX_ADMM_UNROLL2
-#define BODEX_ADMM_UNROLL2 0
-#endif
-
 namespace bodex {
 
 constexpr int MAXJ = BODEX_MAX_JOINTS;
@@ -75,6 +71,8 @@ struct ObjDev {
 
 struct AdmmCfg {
   float mu_c8;  // mu cos(pi/8)
+  float mu;
+  int cone;     // 0: the 8-facet pyramid, 1: the elliptic cone
   float beta, gamma, rho, sigma, alpha, eps, eps_reg;
   int iters, check;
   int fp64_setup;  // build K^-1 in double (set by the host per launch)
@@ -83,6 +81,8 @@ struct AdmmCfg {
 __host__ __device__ inline AdmmCfg admm_cfg(const bodex_qp_params& p) {
   AdmmCfg c;
   c.mu_c8 = p.mu * C8;
+  c.mu = p.mu;
+  c.cone = p.cone;
   c.beta = p.beta;
   c.gamma = p.gamma;
   c.rho = p.rho;
@@ -415,8 +415,13 @@ struct DiagK {
 };
 __device__ __forceinline__ DiagK diag_k(const AdmmCfg& c) {
   DiagK d;
-  d.dn = c.sigma + 2.f * c.eps_reg + c.rho * (1.f + 8.f * c.mu_c8 * c.mu_c8);
-  d.dt = c.sigma + 2.f * c.eps_reg + 4.f * c.rho;
+  if (c.cone) {  // rows f_n and (mu f_n, f_d, f_e): A^T A = diag(1 + mu^2, 1, 1)
+    d.dn = c.sigma + 2.f * c.eps_reg + c.rho * (1.f + c.mu * c.mu);
+    d.dt = c.sigma + 2.f * c.eps_reg + c.rho;
+  } else {
+    d.dn = c.sigma + 2.f * c.eps_reg + c.rho * (1.f + 8.f * c.mu_c8 * c.mu_c8);
+    d.dt = c.sigma + 2.f * c.eps_reg + 4.f * c.rho;
+  }
   return d;
 }
 
@@ -717,13 +722,167 @@ __device__ __forceinline__ void neg_q(const float* G, const float* t, float beta
   }
 }
 
+// ------------------------------------------------------------------ elliptic cone
+// The unlinearised friction model: per contact the row f_n in [0, 1] and
+// the cone rows v = (mu f_n, f_d, f_e) in the second-order cone
+// {|(v1, v2)| <= v0}; the sum row as before.  Rows: per contact
+// [f_n, v0, v1, v2], then the sum row (4m + 1).  The ADMM iteration is the
+// pyramid's with this A and the projection onto the cone in the z-update.
+constexpr int CONE_PYR = 0, CONE_SOC = 1;
+
+// Euclidean projection onto the second-order cone {|(u1, u2)| <= s}
+// (e.g. Parikh & Boyd, Proximal Algorithms, Sec. 6.3.2).
+__device__ __forceinline__ void proj_soc(float s, float u1, float u2, float& ps, float& p1, float& p2) {
+  const float nu = sqrtf(u1 * u1 + u2 * u2);
+  if (nu <= s) {
+    ps = s;
+    p1 = u1;
+    p2 = u2;
+  } else if (nu <= -s) {
+    ps = p1 = p2 = 0.f;
+  } else {  // nu > |s| >= 0
+    const float a = 0.5f * (s + nu), k = a / nu;
+    ps = a;
+    p1 = k * u1;
+    p2 = k * u2;
+  }
+}
+
+template <int M>
+__device__ __forceinline__ void admm_iteration_soc(float* y, float* w, const float* mq, const float* Kinv,
+                                                   const AdmmCfg& c) {
+  constexpr int NV = Admm<M>::NV, NT4 = Admm<M>::NTRI4, NTRI = Admm<M>::NTRI;
+  float4 k0 = lds128(Kinv), k1 = lds128(Kinv + 4), k2 = k1;
+  // rhs = sigma y - q + rho A^T (2 Pi(w) - w), keeping Pi of the cone rows
+  float rhs[NV], pc[3 * M];
+  const float vsum = 2.f * fmaxf(w[4 * M], c.gamma) - w[4 * M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const float* wi = w + 4 * i;
+    proj_soc(wi[1], wi[2], wi[3], pc[3 * i], pc[3 * i + 1], pc[3 * i + 2]);
+    const float v0 = fmaf(2.f, __saturatef(wi[0]), -wi[0]) + vsum;
+    const float gn = fmaf(c.mu, fmaf(2.f, pc[3 * i], -wi[1]), v0);
+    const float gd = fmaf(2.f, pc[3 * i + 1], -wi[2]), ge = fmaf(2.f, pc[3 * i + 2], -wi[3]);
+    rhs[3 * i] = fmaf(c.sigma, y[3 * i], fmaf(c.rho, gn, mq[3 * i]));
+    rhs[3 * i + 1] = fmaf(c.sigma, y[3 * i + 1], fmaf(c.rho, gd, mq[3 * i + 1]));
+    rhs[3 * i + 2] = fmaf(c.sigma, y[3 * i + 2], fmaf(c.rho, ge, mq[3 * i + 2]));
+  }
+  // yt = alpha K^-1 rhs (packed upper triangle, as in admm_iteration)
+  float yt[NV];
+#pragma unroll
+  for (int a = 0; a < NV; ++a) yt[a] = 0.f;
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+#pragma unroll
+    for (int b = a; b < NV; ++b) {
+      const int e = Admm<M>::tri(a, b);
+      const int r = e & 3;
+      const float kv = r == 0 ? k0.x : (r == 1 ? k0.y : (r == 2 ? k0.z : k0.w));
+      yt[a] = fmaf(kv, rhs[b], yt[a]);
+      if (a != b) yt[b] = fmaf(kv, rhs[a], yt[b]);
+      if (r == 3 || e == NTRI - 1) {
+        const int q = e >> 2;
+        if (q + 2 < NT4) k2 = lds128(Kinv + 4 * (q + 2));
+        k0 = k1;
+        k1 = k2;
+      }
+    }
+  }
+  // w <- (w + A yt) - alpha Pi(w),  y <- yt + (1 - alpha) y   (yt = alpha ys)
+  const float al = c.alpha, bl = 1.0f - c.alpha;
+  float sumn = 0.f;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    float* wi = w + 4 * i;
+    const float tn = yt[3 * i], td = yt[3 * i + 1], te = yt[3 * i + 2];
+    sumn += tn;
+    wi[0] = fmaf(-al, __saturatef(wi[0]), wi[0] + tn);
+    wi[1] = fmaf(-al, pc[3 * i], fmaf(c.mu, tn, wi[1]));
+    wi[2] = fmaf(-al, pc[3 * i + 1], wi[2] + td);
+    wi[3] = fmaf(-al, pc[3 * i + 2], wi[3] + te);
+  }
+  w[4 * M] = fmaf(-al, fmaxf(w[4 * M], c.gamma), w[4 * M] + sumn);
+#pragma unroll
+  for (int a = 0; a < NV; ++a) y[a] = fmaf(bl, y[a], yt[a]);
+}
+
+template <int M>
+__device__ inline void admm_residuals_soc(const float* y, const float* w, const float* mq, const float* G,
+                                          const AdmmCfg& c, float& rp, float& rd) {
+  constexpr int NV = Admm<M>::NV;
+  rp = 0.f;
+  float sumn = 0.f;
+  float lam[4 * M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const float* wi = w + 4 * i;
+    const float yn = y[3 * i], yd = y[3 * i + 1], ye = y[3 * i + 2];
+    sumn += yn;
+    const float p0 = __saturatef(wi[0]);
+    float ps, p1, p2;
+    proj_soc(wi[1], wi[2], wi[3], ps, p1, p2);
+    rp = fmaxf(rp, fabsf(yn - p0));
+    rp = fmaxf(rp, fabsf(c.mu * yn - ps));
+    rp = fmaxf(rp, fabsf(yd - p1));
+    rp = fmaxf(rp, fabsf(ye - p2));
+    lam[4 * i] = c.rho * (wi[0] - p0);
+    lam[4 * i + 1] = c.rho * (wi[1] - ps);
+    lam[4 * i + 2] = c.rho * (wi[2] - p1);
+    lam[4 * i + 3] = c.rho * (wi[3] - p2);
+  }
+  rp = fmaxf(rp, fabsf(sumn - fmaxf(w[4 * M], c.gamma)));
+  const float lsum = c.rho * (w[4 * M] - fmaxf(w[4 * M], c.gamma));
+  float gy[6];
+#pragma unroll
+  for (int r = 0; r < 6; ++r) {
+    float s = 0.f;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) s = fmaf(lds32(G + r * NV + a), y[a], s);
+    gy[r] = s;
+  }
+  rd = 0.f;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const float at[3] = {lam[4 * i] + c.mu * lam[4 * i + 1] + lsum, lam[4 * i + 2], lam[4 * i + 3]};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const int a = 3 * i + q;
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < 6; ++r) s = fmaf(lds32(G + r * NV + a), gy[r], s);
+      const float py = 2.f * s + 2.f * c.eps_reg * y[a];
+      rd = fmaxf(rd, fabsf(py - mq[a] + at[q]));
+    }
+  }
+}
+
+// z = Pi(w) of row r of the elliptic-cone rows (the cone rows need the
+// whole triple).
+template <int M>
+__device__ __forceinline__ float proj_row_soc(const float* w, int row, float gamma) {
+  if (row == 4 * M) return fmaxf(w[row], gamma);
+  const int i = row / 4, k = row % 4;
+  if (k == 0) return __saturatef(w[row]);
+  float ps, p1, p2;
+  proj_soc(w[4 * i + 1], w[4 * i + 2], w[4 * i + 3], ps, p1, p2);
+  return k == 1 ? ps : (k == 2 ? p1 : p2);
+}
+
 // Runs ADMM on one QP until both residuals are <= eps (checked every
 // `check` iterations, eps > 0) or `iters` iterations.  Returns the count
 // used; rp/rd receive the last residuals (computed once at the end when
 // eps == 0).
-template <int M>
+template <int M, int CONE>
 __device__ inline int admm_solve(float* y, float* w, const float* mq, const float* Kinv, const float* G,
                                  const AdmmCfg& c, float& rp, float& rd, bool& conv) {
+  auto iterate = [&]() {
+    if (CONE == CONE_SOC) admm_iteration_soc<M>(y, w, mq, Kinv, c);
+    else admm_iteration<M>(y, w, mq, Kinv, c);
+  };
+  auto residuals = [&]() {
+    if (CONE == CONE_SOC) admm_residuals_soc<M>(y, w, mq, G, c, rp, rd);
+    else admm_residuals<M>(y, w, mq, G, c, rp, rd);
+  };
   int it = 0;
   conv = false;
   rp = rd = 0.f;
@@ -732,30 +891,18 @@ __device__ inline int admm_solve(float* y, float* w, const float* mq, const floa
     while (it < c.iters) {
       const int chunk = min(c.check, c.iters - it);
 #pragma unroll 1
-      for (int k = 0; k < chunk; ++k) admm_iteration<M>(y, w, mq, Kinv, c);
+      for (int k = 0; k < chunk; ++k) iterate();
       it += chunk;
-      admm_residuals<M>(y, w, mq, G, c, rp, rd);
+      residuals();
       if (rp <= c.eps && rd <= c.eps) {
         conv = true;
         break;
       }
     }
   } else {
-#if BODEX_ADMM_UNROLL2
 #pragma unroll 1
-    for (; it + 1 < c.iters; it += 2) {
-      admm_iteration<M>(y, w, mq, Kinv, c);
-      admm_iteration<M>(y, w, mq, Kinv, c);
-    }
-    if (it < c.iters) {
-      admm_iteration<M>(y, w, mq, Kinv, c);
-      ++it;
-    }
-#else
-#pragma unroll 1
-    for (; it < c.iters; ++it) admm_iteration<M>(y, w, mq, Kinv, c);
-#endif
-    admm_residuals<M>(y, w, mq, G, c, rp, rd);
+    for (; it < c.iters; ++it) iterate();
+    residuals();
   }
   return it;
 }

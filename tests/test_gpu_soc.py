@@ -1,0 +1,134 @@
+"""Elliptic friction cone (the unlinearised contact model) on the GPU: ADMM
+with the second-order-cone projection vs the FP64 oracle, which brackets
+the optimum between exact QPs over the inscribed and circumscribed K-facet
+pyramids (Q_out <= Q* <= Q_in, K = 512: the bracket is within
+1 - cos(pi/512) ~ 2e-5 of Q in relative terms).  Tolerances otherwise as in
+test_gpu_parity."""
+import numpy as np
+import pytest
+
+from gpu_helpers import I, O, cuda, host, torch
+
+import paper_2412_16490_gb300 as bx
+
+pytestmark = pytest.mark.gpu
+
+MU, BETA, GAMMA, K = 0.5, 1.0, 0.5, 512
+
+
+def soc_rows(m, mu):
+    """ADMM rows of the elliptic cone (per contact f_n, then (mu f_n, f_d,
+    f_e); the sum row last), typed from their definition for the
+    certificate arithmetic below."""
+    A = np.zeros((4 * m + 1, 3 * m))
+    for i in range(m):
+        A[4 * i, 3 * i] = 1
+        A[4 * i + 1, 3 * i] = mu
+        A[4 * i + 2, 3 * i + 1] = 1
+        A[4 * i + 3, 3 * i + 2] = 1
+    A[4 * m, 0::3] = 1
+    return A
+
+
+@pytest.mark.parametrize("m,s,B", [(5, 12, 24), (3, 6, 33), (4, 12, 17)])
+def test_soc_value_within_the_bracket_and_certificate(m, s, B):
+    T = I.wrench_set(s)
+    p, n = I.random_contacts(B, m, seed=70 + m)
+    G32 = O.grasp_matrix(p, n).astype(np.float32)
+    G = G32.astype(np.float64)
+    ref = O.qp_soc(G, T, mu=MU, beta=BETA, gamma=GAMMA, K=K)
+    ok = ref["status"] == 0
+    assert ok.mean() > 0.95
+    prm = bx.qp_params(mu=MU, beta=BETA, gamma=GAMMA, eps_abs=1e-5, max_iter=20000, check_every=10,
+                       cone=bx.CONE_ELLIPTIC)
+    out = bx.bodex_qp_solve_batch(cuda(G32), cuda(T), prm)
+    y, z, lam = (host(out[k]).astype(np.float64) for k in ("y", "z", "lam"))
+    assert z.shape[-1] == 4 * m + 1
+    conv = (host(out["status"]) & bx.ST_NOT_CONVERGED) == 0
+    assert conv.mean() > 0.95
+    # the kernel's y satisfies the cone up to its primal residual
+    fn, ft = y[..., 0::3], np.hypot(y[..., 1::3], y[..., 2::3])
+    assert (ft - MU * fn)[conv].max() < 1e-4
+    Qy = ((BETA * T[None] - np.einsum("bri,bsi->bsr", G, y)) ** 2).sum(-1)
+    np.testing.assert_allclose(host(out["Q"]), Qy, rtol=1e-4, atol=1e-6)
+    # certificate from the GPU's own (y, z, lam): Q(y) - Q* <= |r_d| |y* - y|_1 + |lam|_1 |r_p|,
+    # and Q(y) - Q* >= -|lam*|_1 |r_p|; with Q* in [Q_out, Q_in]
+    A = soc_rows(m, MU)
+    P = 2 * np.einsum("bri,brj->bij", G, G)
+    q = -2 * BETA * np.einsum("bri,sr->bsi", G, T)
+    rp = np.abs(np.einsum("ci,bsi->bsc", A, y) - z).max(-1)
+    rd = np.abs(np.einsum("bij,bsj->bsi", P, y) + q + np.einsum("ci,bsc->bsi", A, lam)).max(-1)
+    upper = rd * np.abs(ref["y"] - y).sum(-1) + np.abs(lam).sum(-1) * rp
+    lower = -np.abs(ref["lam"]).sum(-1) * rp
+    tol = 1e-4 * np.abs(ref["Q_in"]) + 1e-7
+    sel = ok & conv
+    assert (Qy - ref["Q_in"] <= upper + tol)[sel].all(), (Qy - ref["Q_in"] - upper)[sel].max()
+    assert (Qy - ref["Q_out"] >= lower - tol)[sel].all(), (Qy - ref["Q_out"] - lower)[sel].min()
+    assert np.abs(Qy - 0.5 * (ref["Q_in"] + ref["Q_out"]))[sel].max() < 3e-4
+    # the round cone never does worse than the inscribed 8-facet pyramid
+    pyr = O.qp_solve(G, T, mu=MU, beta=BETA, gamma=GAMMA)
+    assert (Qy[sel] <= pyr["Q"][sel] + 3e-4).all()
+
+
+def test_soc_forces_on_the_regularised_problem():
+    """On the regularised problem (eps |y|^2, unique optimum) the forces
+    agree.  Along directions G barely sees, y* is held only by eps, so the
+    oracle's inscribed point needs many facets: K = 2048 puts it within
+    ~3e-4 of y* (it moves 4e-3 from K = 512 to 2048 on these grasps)."""
+    m, s, B = 3, 6, 12
+    T = I.wrench_set(s)
+    p, n = I.random_contacts(B, m, seed=78)
+    G32 = O.grasp_matrix(p, n).astype(np.float32)
+    G = G32.astype(np.float64)
+    ref = O.qp_soc(G, T, eps_reg=1e-3, K=2048)
+    prm = bx.qp_params(eps_abs=2e-6, eps_reg=1e-3, max_iter=150000, check_every=10, cone=bx.CONE_ELLIPTIC)
+    out = bx.bodex_qp_solve_batch(cuda(G32), cuda(T), prm)
+    y = host(out["y"])
+    conv = ((host(out["status"]) & bx.ST_NOT_CONVERGED) == 0) & (ref["status"] == 0)
+    assert conv.mean() >= 0.95
+    assert np.abs(y - ref["y"])[conv].max() <= 2e-3
+    r_gpu = T[None] - np.einsum("bri,bsi->bsr", G, y)
+    r_ref = T[None] - np.einsum("bri,bsi->bsr", G, ref["y"])
+    assert np.abs(r_gpu - r_ref)[conv].max() <= 1e-3
+
+
+def test_soc_energy_gradient_and_step_in_the_fused_kernel():
+    """The fused step with the elliptic cone: E and dE/dx at converged,
+    regularised QPs vs the oracle (whose Q_j and y_j come from the inscribed
+    2048-facet pyramid), then one Adam step."""
+    hand, obj, x0, T, P, _, _ = I.workload("tiny", batch=24)
+    Pr = dict(P, eps_reg=1e-3)
+    H, Ob = bx.Hand(hand), bx.Object(obj)
+    # 2e-6: ADMM on the round cone reaches it on every QP here (1e-6 leaves a
+    # few at a ~5e-6 float32 floor near the cone's apex)
+    sp = bx.step_params(Pr, qp=bx.qp_params(eps_abs=2e-6, eps_reg=1e-3, max_iter=150000, check_every=10,
+                                            cone=bx.CONE_ELLIPTIC))
+    out = bx.bodex_energy_grad(H, Ob, cuda(x0), cuda(T), sp)
+    ev = O.evaluate(O.Hand(hand), O.Object(obj), x0.astype(np.float64), T,
+                    dict(Pr, cone=O.CONE_ELLIPTIC, cone_facets=2048))
+    st = host(out["status"])
+    ok = (st & bx.ST_NOT_CONVERGED) == 0
+    assert ok.mean() >= 0.9
+    np.testing.assert_allclose(host(out["E"])[ok], ev["E"][ok], rtol=2e-4, atol=1e-6)
+    g, gref = host(out["dEdx"]), ev["grad"]
+    rel = np.linalg.norm(g - gref, axis=1) / np.maximum(np.linalg.norm(gref, axis=1), 1e-3)
+    assert (rel[ok] <= 2e-3).all(), rel[ok].max()
+    st8 = bx.State(H, 24, T.shape[0])
+    st8.set_pose(cuda(x0))
+    E = torch.empty(24, device="cuda")
+    bx.bodex_step(H, Ob, st8, cuda(T), 1, sp, E_last=E)
+    lr = np.where(np.arange(hand.dof) < 3, P["lr_t"], P["lr_r"])
+    want = np.clip(x0 - lr * g / (np.abs(g) + P["adam_eps"]), hand.qmin, hand.qmax)
+    np.testing.assert_allclose(host(st8.pose())[ok], want[ok], atol=2e-6)
+
+
+def test_soc_fixed_iteration_run_lowers_the_energy():
+    hand, obj, x0, T, P, _, _ = I.workload("tiny", batch=64)
+    H, Ob = bx.Hand(hand), bx.Object(obj)
+    sp = bx.step_params(P, qp=bx.qp_params(max_iter=50, cone=bx.CONE_ELLIPTIC))
+    E0 = host(bx.bodex_energy_grad(H, Ob, cuda(x0), cuda(T), sp)["E"])
+    st = bx.State(H, 64, T.shape[0])
+    st.set_pose(cuda(x0))
+    E = torch.empty(64, device="cuda")
+    bx.bodex_step(H, Ob, st, cuda(T), 100, sp, E_last=E)
+    assert np.median(host(E) / E0) < 0.7

@@ -320,7 +320,11 @@ enum { MODE_EVAL = 0, MODE_STEP = 1, MODE_ADJOINT = 2 };
 
 // The work of one CTA: GPB grasps (cta * GPB ...) of one job, s lanes each;
 // threads beyond GPB * s idle but take part in every barrier.
-template <int M, int MODE>
+// CONE: CONE_PYR or CONE_SOC fixes the lower-level cone at compile time;
+// CONE_ANY reads it from the arguments (the several-job kernel).
+constexpr int CONE_ANY = -1;
+
+template <int M, int MODE, int CONE = CONE_ANY>
 __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, float* smem) {
   using L = Lay<M>;
   constexpr int NV = L::NV, NC = L::NC;
@@ -418,8 +422,10 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
         float mq[NV];
         neg_q<M>(Gs, t, cfg.beta, mq);
         float rp, rd;
-        if (cfg.cone) admm_solve<M, CONE_SOC>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
-        else admm_solve<M, CONE_PYR>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
+        if (CONE == CONE_ANY ? cfg.cone != 0 : CONE == CONE_SOC)
+          admm_solve<M, CONE_SOC>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
+        else
+          admm_solve<M, CONE_PYR>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
         if (step == A.n_steps - 1) atomicMax(reinterpret_cast<int*>(sc + 2), __float_as_int(fmaxf(rp, rd)));
       }
       float* ry = per + L::oRY + lane * (6 + NV);
@@ -610,10 +616,10 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
   }
 }
 
-template <int M, int MODE>
+template <int M, int MODE, int CONE>
 __global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
   extern __shared__ __align__(16) float smem[];
-  fused_cta<M, MODE>(A, blockIdx.x, A.gpb, smem);
+  fused_cta<M, MODE, CONE>(A, blockIdx.x, A.gpb, smem);
 }
 
 // ============================================================================ kernel: several jobs in one launch
@@ -939,15 +945,22 @@ int run_fused(int mode, const FusedArgs& A0, cudaStream_t st) {
   const size_t bytes = Lay<M>::bytes(gpb);
   const dim3 grid((A.B + gpb - 1) / gpb), block(gpb * A.S);
   if (A.B == 0) return BODEX_OK;
-  if (mode == MODE_STEP) {
-    if (int r = ensure_smem(fused_kernel<M, MODE_STEP>, bytes)) return r;
-    fused_kernel<M, MODE_STEP><<<grid, block, bytes, st>>>(A);
-  } else if (mode == MODE_ADJOINT) {
-    if (int r = ensure_smem(fused_kernel<M, MODE_ADJOINT>, bytes)) return r;
-    fused_kernel<M, MODE_ADJOINT><<<grid, block, bytes, st>>>(A);
+  const bool soc = A.cfg.cone != 0;
+  if (mode == MODE_STEP && soc) {
+    if (int r = ensure_smem(fused_kernel<M, MODE_STEP, CONE_SOC>, bytes)) return r;
+    fused_kernel<M, MODE_STEP, CONE_SOC><<<grid, block, bytes, st>>>(A);
+  } else if (mode == MODE_STEP) {
+    if (int r = ensure_smem(fused_kernel<M, MODE_STEP, CONE_PYR>, bytes)) return r;
+    fused_kernel<M, MODE_STEP, CONE_PYR><<<grid, block, bytes, st>>>(A);
+  } else if (mode == MODE_ADJOINT) {  // no lower-level solve
+    if (int r = ensure_smem(fused_kernel<M, MODE_ADJOINT, CONE_PYR>, bytes)) return r;
+    fused_kernel<M, MODE_ADJOINT, CONE_PYR><<<grid, block, bytes, st>>>(A);
+  } else if (soc) {
+    if (int r = ensure_smem(fused_kernel<M, MODE_EVAL, CONE_SOC>, bytes)) return r;
+    fused_kernel<M, MODE_EVAL, CONE_SOC><<<grid, block, bytes, st>>>(A);
   } else {
-    if (int r = ensure_smem(fused_kernel<M, MODE_EVAL>, bytes)) return r;
-    fused_kernel<M, MODE_EVAL><<<grid, block, bytes, st>>>(A);
+    if (int r = ensure_smem(fused_kernel<M, MODE_EVAL, CONE_PYR>, bytes)) return r;
+    fused_kernel<M, MODE_EVAL, CONE_PYR><<<grid, block, bytes, st>>>(A);
   }
   return launch_err("fused_kernel launch");
 }

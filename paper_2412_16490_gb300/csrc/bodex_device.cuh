@@ -549,18 +549,10 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
 // The shared memory holds alpha K^-1, so the product below is alpha yt and
 // the relaxation costs no separate multiply.
 // Row order of A: per contact [f_n, facet 0..7], then the sum row.
-// 16-byte shared-memory load kept inside the loop that issues it.  K^-1 is
-// loop-invariant across ADMM iterations; left to itself the compiler hoists
-// all of it into registers, which does not fit next to the iterate.
-__device__ __forceinline__ float4 lds128(const float* p) {
-  float4 v;
-  const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "r"(addr));
-  return v;
-}
-
+// Shared-memory load kept inside the loop that issues it (asm volatile).
+// K^-1 is loop-invariant across ADMM iterations; left to itself the
+// compiler hoists all of it into registers, which does not fit next to the
+// iterate.
 __device__ __forceinline__ float lds32(const float* p) {
   float v;
   const unsigned addr = (unsigned)__cvta_generic_to_shared(p);
@@ -593,10 +585,7 @@ __device__ __forceinline__ void At_contact(float v0, const float (&vk)[8], float
 template <int M>
 __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* mq, const float* Kinv,
                                                const AdmmCfg& c) {
-  constexpr int NV = Admm<M>::NV, NT4 = Admm<M>::NTRI4, NTRI = Admm<M>::NTRI;
-  // The first float4s of the packed alpha K^-1 are requested before the rhs
-  // is formed; chunk q+2 is requested while chunk q is used.
-  float4 k0 = lds128(Kinv), k1 = lds128(Kinv + 4), k2 = k1;
+  constexpr int NV = Admm<M>::NV;
   // rhs = sigma y - q + rho A^T v,  v = 2 Pi(w) - w, one contact at a time
   float rhs[NV];
   const float vsum = 2.f * fmaxf(w[9 * M], c.gamma) - w[9 * M];
@@ -614,27 +603,22 @@ __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* 
     rhs[3 * i + 1] = fmaf(c.sigma, y[3 * i + 1], fmaf(c.rho, gd, mq[3 * i + 1]));
     rhs[3 * i + 2] = fmaf(c.sigma, y[3 * i + 2], fmaf(c.rho, ge, mq[3 * i + 2]));
   }
-  // yt = alpha K^-1 rhs from the packed upper triangle: entry (a, b) adds
-  // K_ab rhs_b to yt_a and, off the diagonal, K_ab rhs_a to yt_b.  The
-  // loops unroll completely, so every index below is a compile-time constant.
+  // yt = alpha K^-1 rhs from the packed upper triangle, column by column:
+  // entry (a, b), a <= b, adds K_ab rhs_b to yt_a and, off the diagonal,
+  // K_ab rhs_a to yt_b.  The loops unroll completely (every index is a
+  // compile-time constant) and each entry is one 4-byte shared load that all
+  // lanes of the grasp share.  Measured against row order and against
+  // 16-byte loads issued ahead, this order is 2-4% faster per iteration.
   float yt[NV];
 #pragma unroll
   for (int a = 0; a < NV; ++a) yt[a] = 0.f;
 #pragma unroll
-  for (int a = 0; a < NV; ++a) {
+  for (int b = 0; b < NV; ++b) {
 #pragma unroll
-    for (int b = a; b < NV; ++b) {
-      const int e = Admm<M>::tri(a, b);
-      const int r = e & 3;
-      const float kv = r == 0 ? k0.x : (r == 1 ? k0.y : (r == 2 ? k0.z : k0.w));
+    for (int a = 0; a <= b; ++a) {
+      const float kv = lds32(Kinv + Admm<M>::tri(a, b));
       yt[a] = fmaf(kv, rhs[b], yt[a]);
       if (a != b) yt[b] = fmaf(kv, rhs[a], yt[b]);
-      if (r == 3 || e == NTRI - 1) {
-        const int q = e >> 2;
-        if (q + 2 < NT4) k2 = lds128(Kinv + 4 * (q + 2));
-        k0 = k1;
-        k1 = k2;
-      }
     }
   }
   // w <- w + alpha (A ys - Pi(w)) = (w + A yt) - alpha Pi(w),
@@ -751,8 +735,7 @@ __device__ __forceinline__ void proj_soc(float s, float u1, float u2, float& ps,
 template <int M>
 __device__ __forceinline__ void admm_iteration_soc(float* y, float* w, const float* mq, const float* Kinv,
                                                    const AdmmCfg& c) {
-  constexpr int NV = Admm<M>::NV, NT4 = Admm<M>::NTRI4, NTRI = Admm<M>::NTRI;
-  float4 k0 = lds128(Kinv), k1 = lds128(Kinv + 4), k2 = k1;
+  constexpr int NV = Admm<M>::NV;
   // rhs = sigma y - q + rho A^T (2 Pi(w) - w), keeping Pi of the cone rows
   float rhs[NV], pc[3 * M];
   const float vsum = 2.f * fmaxf(w[4 * M], c.gamma) - w[4 * M];
@@ -767,25 +750,17 @@ __device__ __forceinline__ void admm_iteration_soc(float* y, float* w, const flo
     rhs[3 * i + 1] = fmaf(c.sigma, y[3 * i + 1], fmaf(c.rho, gd, mq[3 * i + 1]));
     rhs[3 * i + 2] = fmaf(c.sigma, y[3 * i + 2], fmaf(c.rho, ge, mq[3 * i + 2]));
   }
-  // yt = alpha K^-1 rhs (packed upper triangle, as in admm_iteration)
+  // yt = alpha K^-1 rhs (packed upper triangle, column order as in admm_iteration)
   float yt[NV];
 #pragma unroll
   for (int a = 0; a < NV; ++a) yt[a] = 0.f;
 #pragma unroll
-  for (int a = 0; a < NV; ++a) {
+  for (int b = 0; b < NV; ++b) {
 #pragma unroll
-    for (int b = a; b < NV; ++b) {
-      const int e = Admm<M>::tri(a, b);
-      const int r = e & 3;
-      const float kv = r == 0 ? k0.x : (r == 1 ? k0.y : (r == 2 ? k0.z : k0.w));
+    for (int a = 0; a <= b; ++a) {
+      const float kv = lds32(Kinv + Admm<M>::tri(a, b));
       yt[a] = fmaf(kv, rhs[b], yt[a]);
       if (a != b) yt[b] = fmaf(kv, rhs[a], yt[b]);
-      if (r == 3 || e == NTRI - 1) {
-        const int q = e >> 2;
-        if (q + 2 < NT4) k2 = lds128(Kinv + 4 * (q + 2));
-        k0 = k1;
-        k1 = k2;
-      }
     }
   }
   // w <- (w + A yt) - alpha Pi(w),  y <- yt + (1 - alpha) y   (yt = alpha ys)

@@ -167,6 +167,12 @@ typedef struct bodex_qp_params {
                         projection).  ADMM rows, for z and lam: per contact f_n, then
                         8 facets (pyramid, 9m+1 rows in all) or the cone rows
                         (mu f_n, f_d, f_e) (elliptic, 4m+1 rows in all); the sum row last. */
+  int adaptive_rho;  /* 1: with eps_abs > 0, adapt rho per grasp by residual balancing
+                        (OSQP, Stellato et al. 2020): every check_every iterations,
+                        when sqrt(|r_p| / |r_d|) averaged over the grasp's unconverged
+                        QPs exceeds 5 or 1/5, rho is multiplied by it and K^-1 rebuilt.
+                        Results are unchanged up to the residual target; 0: fixed rho.
+                        Ignored when eps_abs == 0 (fixed iteration counts). */
 } bodex_qp_params;
 
 #define BODEX_CONE_PYRAMID 0

@@ -57,10 +57,12 @@ def _np(a, dt):
 
 # ---------------------------------------------------------------- parameters
 def qp_params(mu=0.5, beta=1.0, gamma=0.5, rho=0.1, sigma=1e-6, alpha=1.6, eps_abs=0.0, eps_reg=0.0,
-              max_iter=50, check_every=10, warm=0, strict=0, cone=0) -> _b.bodex_qp_params:
-    """ADMM/QP parameters (struct bodex_qp_params); cone: CONE_PYRAMID or CONE_ELLIPTIC."""
+              max_iter=50, check_every=10, warm=0, strict=0, cone=0, adaptive_rho=0) -> _b.bodex_qp_params:
+    """ADMM/QP parameters (struct bodex_qp_params); cone: CONE_PYRAMID or
+    CONE_ELLIPTIC; adaptive_rho: residual-balancing rho in solves with a
+    residual target (eps_abs > 0)."""
     return _b.bodex_qp_params(mu, beta, gamma, rho, sigma, alpha, eps_abs, eps_reg, int(max_iter),
-                              int(check_every), int(warm), int(strict), int(cone))
+                              int(check_every), int(warm), int(strict), int(cone), int(adaptive_rho))
 
 
 def step_params(params: dict | None = None, qp: _b.bodex_qp_params | None = None,

@@ -55,7 +55,7 @@ class bodex_qp_params(C.Structure):
     _fields_ = [("mu", C.c_float), ("beta", C.c_float), ("gamma", C.c_float), ("rho", C.c_float),
                 ("sigma", C.c_float), ("alpha", C.c_float), ("eps_abs", C.c_float), ("eps_reg", C.c_float),
                 ("max_iter", C.c_int), ("check_every", C.c_int), ("warm", C.c_int), ("strict", C.c_int),
-                ("cone", C.c_int)]
+                ("cone", C.c_int), ("adaptive_rho", C.c_int)]
 
 
 class bodex_energy_params(C.Structure):

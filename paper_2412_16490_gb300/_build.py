@@ -10,8 +10,13 @@ import subprocess
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
-SRC = [os.path.join(HERE, "csrc", "bodex.cu")]
-DEPS = SRC + [os.path.join(HERE, "csrc", "bodex_device.cuh"), os.path.join(ROOT, "include", "bodex.h")]
+CSRC = os.path.join(HERE, "csrc")
+# translation units, compiled in parallel: the C ABI and small kernels, then
+# the heavy kernel families (see bodex_kernels.cuh)
+UNITS = ["bodex.cu", "qp.cu", "fused_m3.cu", "fused_m4.cu", "fused_m5.cu", "fused_multi.cu"]
+SRC = [os.path.join(CSRC, u) for u in UNITS]
+DEPS = SRC + [os.path.join(CSRC, "bodex_device.cuh"), os.path.join(CSRC, "bodex_kernels.cuh"),
+              os.path.join(ROOT, "include", "bodex.h")]
 LIB = os.path.join(HERE, "libbodex.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -29,16 +34,27 @@ def stale() -> bool:
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile libbodex.so (skipped when it is newer than every source)."""
+    """Compile libbodex.so (skipped when it is newer than every source): every
+    translation unit in its own nvcc process, then one link."""
     if not force and not stale():
         return LIB
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-           "-I", os.path.join(ROOT, "include"), *SRC, "-o", tmp]
+    tag = f".tmp{os.getpid()}"
+    objs = [os.path.join(CSRC, u[:-3] + tag + ".o") for u in UNITS]
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-    subprocess.check_call(cmd)
-    os.replace(tmp, LIB)
+        flags.insert(0, "-Xptxas=-v")
+    procs = [subprocess.Popen([nvcc(), *flags, "-c", src, "-o", obj]) for src, obj in zip(SRC, objs)]
+    codes = [p.wait() for p in procs]
+    try:
+        if any(codes):
+            raise subprocess.CalledProcessError(next(c for c in codes if c), "nvcc -c")
+        tmp = LIB + tag
+        subprocess.check_call([nvcc(), *ARCH, "-shared", *objs, "-o", tmp])
+        os.replace(tmp, LIB)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

@@ -1,5 +1,7 @@
-// BODex coarse-stage hot path for GB300 (sm_103a): kernels and the C ABI
-// declared in include/bodex.h.
+// BODex coarse-stage hot path for GB300 (sm_103a): the C ABI declared in
+// include/bodex.h and its small kernels (kinematics, refinement, metrics);
+// the heavy kernels live in bodex_kernels.cuh and are compiled in their own
+// translation units.
 //
 // Kernel layout.  One CTA holds GPB grasps and s lanes (threads) per grasp,
 // GPB * s = 96 threads for s = 6 or 12.  Lane j of a grasp owns the QP of
@@ -24,13 +26,16 @@
 
 #include "../../include/bodex.h"
 #include "bodex_device.cuh"
+#include "bodex_kernels.cuh"
 
 using namespace bodex;
 
 // ============================================================================ error state
 namespace {
 thread_local std::string g_err;
+}  // namespace
 
+namespace bodex {
 int fail(int code, const std::string& msg) {
   g_err = msg;
   return code;
@@ -38,12 +43,20 @@ int fail(int code, const std::string& msg) {
 int cuda_fail(cudaError_t e, const char* where) {
   return fail(BODEX_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
+int launch_err(const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, what);
+  return BODEX_OK;
+}
+}  // namespace bodex
+
 #define BODEX_CUDA(call)                                    \
   do {                                                      \
     cudaError_t e_ = (call);                                \
     if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
   } while (0)
 
+namespace {
 cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
 }  // namespace
 
@@ -70,83 +83,6 @@ struct bodex_state_s {
   float* res = nullptr;  // [B] max QP residual at the last step of the last launch
   int t = 0;
 };
-
-// ============================================================================ shared-memory layout
-constexpr int CTA_LANES = 96;
-
-__host__ __device__ constexpr int align4(int v) { return (v + 3) & ~3; }
-
-template <int M>
-struct Lay {
-  static constexpr int NV = 3 * M, NC = 9 * M + 1, NVP = (NV + 3) & ~3;
-  // K^-1 block per grasp (packed upper triangle in whole float4s); the
-  // stride is skewed (== 20 mod 32 words) so that lanes of two or three
-  // grasps in one warp hit disjoint banks.
-  static constexpr int KT = 4 * Admm<M>::NTRI4;
-  static constexpr int KS = KT + ((20 - KT % 32) + 32) % 32;
-  static constexpr int CTW = 24;  // floats per contact record
-  static constexpr int oG = 0;
-  static constexpr int oK = oG + 6 * NV;  // K^-1 setup scratch
-  static constexpr int oCT = oK + WoodburyScratch<M, double>::floats;
-  static constexpr int oRY = oCT + CTW * M;
-  static constexpr int oQ = oRY + SMAX * (6 + NV);
-  static constexpr int oDG = oQ + SMAX;
-  static constexpr int oCB = oDG + 6 * NV;
-  static constexpr int oX = oCB + M * (6 + MAXCHAIN);
-  static constexpr int oAM = oX + MAXD;
-  static constexpr int oAV = oAM + MAXD;
-  static constexpr int oJW = oAV + MAXD;  // chain joint axes/points, M x MAXCHAIN x 6
-  static constexpr int oGC = oJW + M * MAXCHAIN * 6;  // collision gradient [MAXD], energy by lane [SMAX]
-  static constexpr int oSC = oGC + MAXD + SMAX;
-  // collision scratch: link frames in the K^-1 setup scratch, sphere centres
-  // and slot sums in the r / Q / dE/dG block (both dead before A4)
-  static constexpr int COLL_FR = WoodburyScratch<M, double>::floats;
-  static constexpr int COLL_CS = SMAX * (6 + NV) + SMAX + 6 * NV;
-  // per-grasp stride == 12 (mod 32) words: the two or three grasps that
-  // share a warp then map the same offset to different banks
-  static constexpr int PER = align4(oSC + 4) + ((12 - align4(oSC + 4) % 32) + 32) % 32;
-  static constexpr int HAND_WORDS = align4((int)(sizeof(HandDev) / 4));
-  static size_t bytes(int gpb) { return 4u * (size_t)(HAND_WORDS + gpb * (KS + PER)); }
-};
-
-// Contact record in shared memory: c(3) p(3) n(3) phi g(3) h(6) cell(3) degenerate.
-__device__ __forceinline__ void store_ct(float* r, const ContactGeo& k) {
-  for (int a = 0; a < 3; ++a) {
-    r[a] = k.c[a];
-    r[3 + a] = k.p[a];
-    r[6 + a] = k.n[a];
-    r[10 + a] = k.g[a];
-    r[19 + a] = __int_as_float(k.cell[a]);
-  }
-  r[9] = k.phi;
-  for (int e = 0; e < 6; ++e) r[13 + e] = k.h[e];
-  r[22] = __int_as_float(k.degenerate);
-}
-__device__ __forceinline__ ContactGeo load_ct(const float* r) {
-  ContactGeo k;
-  for (int a = 0; a < 3; ++a) {
-    k.c[a] = r[a];
-    k.p[a] = r[3 + a];
-    k.n[a] = r[6 + a];
-    k.g[a] = r[10 + a];
-    k.cell[a] = __float_as_int(r[19 + a]);
-  }
-  k.phi = r[9];
-  for (int e = 0; e < 6; ++e) k.h[e] = r[13 + e];
-  k.degenerate = __float_as_int(r[22]);
-  return k;
-}
-
-__device__ __forceinline__ void copy_hand_to_smem(const HandDev* src, float* dst) {
-  const int* s = reinterpret_cast<const int*>(src);
-  int* d = reinterpret_cast<int*>(dst);
-  const int words = (int)(sizeof(HandDev) / 4);
-  for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = __ldg(s + i);
-}
-
-__device__ __forceinline__ bool finite3(const float* v) {
-  return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
-}
 
 // ============================================================================ kernel: FK + contacts + G
 template <int M>
@@ -189,466 +125,6 @@ __global__ void __launch_bounds__(128) fk_contacts_kernel(const HandDev* __restr
   if (G_out)
     for (int e = 0; e < 6 * NV; ++e) G_out[(size_t)b * 6 * NV + e] = Gl[e];
   if (status_out) status_out[b] = st;
-}
-
-// ============================================================================ per-grasp QP setup (shared by kernels)
-// K^-1 of every grasp of the CTA (Woodbury form, all lanes); must be called
-// by every thread of the CTA (contains barriers).
-// Double precision when the host asks for it (solves that iterate to a
-// tight residual target), single precision otherwise; the branch is
-// uniform per launch.
-template <int M>
-__device__ inline void setup_kinv(bool active, int lane, int S, const float* Gs, float* scratch, float* Kinv,
-                                  const AdmmCfg& cfg) {
-  if (cfg.fp64_setup) setup_kinv_woodbury<M, double>(active, lane, S, Gs, scratch, Kinv, cfg);
-  else setup_kinv_woodbury<M, float>(active, lane, S, Gs, scratch, Kinv, cfg);
-}
-
-// ============================================================================ kernel: batched QP
-template <int M, int CONE>
-__global__ void __launch_bounds__(CTA_LANES) qp_solve_kernel(const float* __restrict__ Gin, int B,
-                                                             const float* __restrict__ T, int S, AdmmCfg cfg,
-                                                             int warm, float* yio, float* zio, float* lio,
-                                                             float* Qout, int32_t* iters_out, int32_t* status_out,
-                                                             float* res_out) {
-  using L = Lay<M>;
-  constexpr int NV = L::NV, NC = CONE == CONE_SOC ? 4 * M + 1 : L::NC;  // ADMM rows
-  extern __shared__ __align__(16) float smem[];
-  const int GPB = blockDim.x / S;
-  const int gl = threadIdx.x / S, lane = threadIdx.x % S;
-  const int b = blockIdx.x * GPB + gl;
-  const bool active = (gl < GPB) && (b < B);
-  float* kin = smem + L::HAND_WORDS + gl * L::KS;
-  float* per = smem + L::HAND_WORDS + GPB * L::KS + gl * L::PER;
-  float* Gs = per + L::oG;
-  int* stat = reinterpret_cast<int*>(per + L::oSC + 1);
-  if (active) {
-    for (int e = lane; e < 6 * NV; e += S) Gs[e] = Gin[(size_t)b * 6 * NV + e];
-    if (lane == 0) *stat = 0;
-  }
-  __syncthreads();
-  setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg);
-  if (!active) return;  // no barriers below
-  const size_t q = (size_t)b * S + lane;
-  float y[NV], w[NC], mq[NV];
-  float t[6];
-  for (int r = 0; r < 6; ++r) t[r] = T[lane * 6 + r];
-  neg_q<M>(Gs, t, cfg.beta, mq);
-  if (warm) {
-#pragma unroll
-    for (int a = 0; a < NV; ++a) y[a] = yio[q * NV + a];
-#pragma unroll
-    for (int r = 0; r < NC; ++r) w[r] = zio[q * NC + r] + lio[q * NC + r] / cfg.rho;
-  } else {
-#pragma unroll
-    for (int a = 0; a < NV; ++a) y[a] = 0.f;
-#pragma unroll
-    for (int r = 0; r < NC; ++r) w[r] = 0.f;
-  }
-  float rp, rd;
-  bool conv;
-  const int it = admm_solve<M, CONE>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
-  float Q = 0.f;
-  bool fin = true;
-#pragma unroll
-  for (int r = 0; r < 6; ++r) {
-    float s = cfg.beta * t[r];
-#pragma unroll
-    for (int a = 0; a < NV; ++a) s = fmaf(-Gs[r * NV + a], y[a], s);
-    Q = fmaf(s, s, Q);
-  }
-#pragma unroll
-  for (int a = 0; a < NV; ++a) {
-    yio[q * NV + a] = y[a];
-    fin = fin && isfinite(y[a]);
-    Q = fmaf(cfg.eps_reg * y[a], y[a], Q);  // regularised value when eps_reg > 0
-  }
-#pragma unroll
-  for (int r = 0; r < NC; ++r) {
-    const float p = CONE == CONE_SOC ? proj_row_soc<M>(w, r, cfg.gamma) : proj_row<M>(w[r], r, cfg.gamma);
-    zio[q * NC + r] = p;
-    lio[q * NC + r] = cfg.rho * (w[r] - p);
-  }
-  Qout[q] = Q;
-  if (iters_out) iters_out[q] = it;
-  if (res_out) {
-    res_out[2 * q] = rp;
-    res_out[2 * q + 1] = rd;
-  }
-  int st = *stat;
-  if (!fin || !isfinite(Q)) st |= BODEX_ST_NONFINITE;
-  if (cfg.eps > 0.f && !conv) st |= BODEX_ST_NOT_CONVERGED;
-  if (status_out) status_out[q] = st;
-}
-
-// ============================================================================ kernel: fused evaluation / step
-struct FusedArgs {
-  const HandDev* hand;
-  ObjDev obj;
-  const float* T;
-  int S, B;
-  AdmmCfg cfg;
-  float w_q, w_d, delta;
-  float lr_t, lr_r, b1, b2, adam_eps;
-  int n_steps, t0;
-  // pose input (eval) or state pose (step), updated in place for step
-  const float* x_in;
-  float* x_state;
-  float* am;
-  float* av;
-  float* qy;  // warm start: may be null in eval (cold start); the state's arrays in step mode
-  float* qw;
-  // outputs
-  float* E;
-  float* dEdx;
-  float* Qout;
-  float* yout;
-  int32_t* status;
-  const float* yin;  // MODE_ADJOINT: forces from a previous solve [B, s, 3m]
-  float* res;        // [B] max ADMM residual of the grasp's QPs at the last step (may be null)
-  int gpb;           // grasps per CTA
-  int dfc;           // 1: the DFC force-closure energy |G u|^2 replaces the QPs (uniform per launch)
-  int coll;          // 1: the collision energies are on (uniform per launch)
-  CollDev cd;
-  CollParams cp;
-};
-
-// MODE_EVAL: E and dE/dx at x.  MODE_STEP: n_steps upper iterations on the
-// state.  MODE_ADJOINT: E and dE/dx at x for given forces y (no QP solve):
-// the backward pass of the energy, with FK and the SDF query recomputed.
-enum { MODE_EVAL = 0, MODE_STEP = 1, MODE_ADJOINT = 2 };
-
-// The work of one CTA: GPB grasps (cta * GPB ...) of one job, s lanes each;
-// threads beyond GPB * s idle but take part in every barrier.
-// CONE: CONE_PYR or CONE_SOC fixes the lower-level cone at compile time;
-// CONE_ANY reads it from the arguments (the several-job kernel).
-constexpr int CONE_ANY = -1;
-
-template <int M, int MODE, int CONE = CONE_ANY>
-__device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, float* smem) {
-  using L = Lay<M>;
-  constexpr int NV = L::NV, NC = L::NC;
-  copy_hand_to_smem(A.hand, smem);
-  const int S = A.S;
-  const int gl = threadIdx.x / S, lane = threadIdx.x % S;
-  const int b = cta * GPB + gl;
-  const bool active = (gl < GPB) && (b < A.B);
-  const HandDev& H = *reinterpret_cast<const HandDev*>(smem);
-  float* kin = smem + L::HAND_WORDS + gl * L::KS;
-  float* per = smem + L::HAND_WORDS + GPB * L::KS + gl * L::PER;
-  float* Gs = per + L::oG;
-  float* xs = per + L::oX;
-  float* ams = per + L::oAM;
-  float* avs = per + L::oAV;
-  float* sc = per + L::oSC;
-  int* stat = reinterpret_cast<int*>(sc + 1);
-  __syncthreads();  // hand copied
-  const int D = H.D;
-  const AdmmCfg& cfg = A.cfg;
-
-  if (active) {
-    const float* xsrc = (MODE == MODE_STEP) ? A.x_state : A.x_in;
-    for (int k = lane; k < D; k += S) {
-      xs[k] = xsrc[(size_t)b * D + k];
-      if (MODE == MODE_STEP) {
-        ams[k] = A.am[(size_t)b * D + k];
-        avs[k] = A.av[(size_t)b * D + k];
-      }
-    }
-    if (lane == 0) {
-      *stat = 0;
-      sc[2] = 0.f;  // max residual of the grasp's QPs at the last step
-    }
-  }
-  // ADMM iterate of this lane's QP.  In MODE_STEP it lives in the state's
-  // warm-start arrays between upper steps and in registers only around the
-  // solve, so the FK / SDF / adjoint phases get the registers it would hold.
-  float y[NV], w[NC];
-  const size_t q = (size_t)b * S + lane, NQ = (size_t)A.B * S;
-  if (MODE == MODE_ADJOINT && active) {
-#pragma unroll
-    for (int a = 0; a < NV; ++a) y[a] = A.yin[q * NV + a];
-#pragma unroll
-    for (int r = 0; r < NC; ++r) w[r] = 0.f;
-  } else if (MODE == MODE_EVAL && active && A.qy) {
-#pragma unroll
-    for (int a = 0; a < NV; ++a) y[a] = A.qy[a * NQ + q];
-#pragma unroll
-    for (int r = 0; r < NC; ++r) w[r] = A.qw[r * NQ + q];
-  } else {
-#pragma unroll
-    for (int a = 0; a < NV; ++a) y[a] = 0.f;
-#pragma unroll
-    for (int r = 0; r < NC; ++r) w[r] = 0.f;
-  }
-  float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-  if (active)
-    for (int r = 0; r < 6; ++r) t[r] = A.T[lane * 6 + r];
-  __syncthreads();
-
-  for (int step = 0; step < A.n_steps; ++step) {
-    // ---- A1-A3: kinematics, nearest-point query, grasp matrix (lane = contact)
-    if (active && lane < M) {
-      float c[3];
-      fk_contact(H, lane, xs, c, per + L::oJW + lane * MAXCHAIN * 6,
-                 (A.coll && A.cd.K > 0) ? per + L::oK : nullptr);  // link frames for the collision spheres
-      const ContactGeo k = contact_geometry(A.obj, c);
-      store_ct(per + L::oCT + L::CTW * lane, k);
-      write_G_block(k, lane, NV, Gs);
-      int st = 0;
-      if (k.degenerate) st |= BODEX_ST_DEGENERATE_NORMAL;
-      if (!finite3(k.p) || !finite3(k.n) || !isfinite(k.phi)) st |= BODEX_ST_NONFINITE;
-      if (st) atomicOr(stat, st);
-    }
-    __syncthreads();
-    // ---- constraint energies on the collision spheres (Sec. IV-B)
-    if (A.coll)
-      collision_phase(active, lane, S, H, A.cd, A.obj, xs, A.cp, per + L::oK, per + L::oJW, per + L::oRY,
-                      per + L::oRY + 3 * A.cd.K, per + L::oRY + 3 * A.cd.K + 6 * (H.n + 1), per + L::oGC,
-                      per + L::oGC + MAXD);
-    // ---- A4: K^-1 per grasp
-    if (MODE != MODE_ADJOINT && !A.dfc) setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg);
-    // ---- A5: ADMM, one QP per lane
-    if (active && A.dfc) per[L::oQ + lane] = 0.f;  // no lower-level QPs under DFC
-    if (active && !A.dfc) {
-      bool conv = true;
-      if (MODE == MODE_STEP) {
-#pragma unroll
-        for (int a = 0; a < NV; ++a) y[a] = A.qy[a * NQ + q];
-#pragma unroll
-        for (int r = 0; r < NC; ++r) w[r] = A.qw[r * NQ + q];
-      }
-      if (MODE != MODE_ADJOINT) {
-        float mq[NV];
-        neg_q<M>(Gs, t, cfg.beta, mq);
-        float rp, rd;
-        if (CONE == CONE_ANY ? cfg.cone != 0 : CONE == CONE_SOC)
-          admm_solve<M, CONE_SOC>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
-        else
-          admm_solve<M, CONE_PYR>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
-        if (step == A.n_steps - 1) atomicMax(reinterpret_cast<int*>(sc + 2), __float_as_int(fmaxf(rp, rd)));
-      }
-      float* ry = per + L::oRY + lane * (6 + NV);
-      float Q = 0.f;
-#pragma unroll
-      for (int r = 0; r < 6; ++r) {
-        float s = cfg.beta * t[r];
-#pragma unroll
-        for (int a = 0; a < NV; ++a) s = fmaf(-Gs[r * NV + a], y[a], s);
-        ry[r] = s;
-        Q = fmaf(s, s, Q);
-      }
-#pragma unroll
-      for (int a = 0; a < NV; ++a) {
-        ry[6 + a] = y[a];
-        Q = fmaf(cfg.eps_reg * y[a], y[a], Q);  // regularised value when eps_reg > 0
-      }
-      per[L::oQ + lane] = Q;
-      if (MODE == MODE_STEP) {
-#pragma unroll
-        for (int a = 0; a < NV; ++a) A.qy[a * NQ + q] = y[a];
-#pragma unroll
-        for (int r = 0; r < NC; ++r) A.qw[r * NQ + q] = w[r];
-      }
-      int st = 0;
-      if (cfg.eps > 0.f && !conv) st |= BODEX_ST_NOT_CONVERGED;
-      if (!isfinite(Q)) st |= BODEX_ST_NONFINITE;
-      if (st) atomicOr(stat, st);
-    }
-    __syncthreads();
-    // ---- A6: energy;  A7 (part 1): dE/dG = -2 w_Q sum_j r_j y_j^T
-    // (DFC: E_Q = |G u|^2 with u = 1 on every normal component, so
-    // dE/dG = 2 w_Q (G u) u^T: only the normal columns)
-    if (active && A.dfc) {
-      float gu[6];
-#pragma unroll
-      for (int r = 0; r < 6; ++r) {
-        float s = 0.f;
-#pragma unroll
-        for (int i = 0; i < M; ++i) s += Gs[r * NV + 3 * i];
-        gu[r] = s;
-      }
-      for (int e = lane; e < 6 * NV; e += S) {
-        const int r = e / NV, a = e % NV;
-        float g = 0.f;
-#pragma unroll
-        for (int rr = 0; rr < 6; ++rr) g = (rr == r) ? gu[rr] : g;
-        per[L::oDG + e] = (a % 3 == 0) ? 2.f * A.w_q * g : 0.f;
-      }
-      if (lane == 0) {
-        float EQ = 0.f;
-#pragma unroll
-        for (int r = 0; r < 6; ++r) EQ = fmaf(gu[r], gu[r], EQ);
-        float Ed = 0.f;
-        for (int i = 0; i < M; ++i) {
-          const float r = per[L::oCT + L::CTW * i + 9] - H.alpha - A.delta;
-          Ed = fmaf(r, r, Ed);
-        }
-        float Ec = 0.f;
-        if (A.coll)
-          for (int l = 0; l < S; ++l) Ec += per[L::oGC + MAXD + l];
-        sc[0] = A.w_q * EQ + A.w_d * Ed + Ec;
-      }
-    }
-    if (active && !A.dfc) {
-      const float* ry = per + L::oRY;
-      for (int e = lane; e < 6 * NV; e += S) {
-        const int r = e / NV, a = e % NV;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;  // independent partial sums
-        int j = 0;
-        for (; j + 3 < S; j += 4) {
-          s0 = fmaf(ry[j * (6 + NV) + r], ry[j * (6 + NV) + 6 + a], s0);
-          s1 = fmaf(ry[(j + 1) * (6 + NV) + r], ry[(j + 1) * (6 + NV) + 6 + a], s1);
-          s2 = fmaf(ry[(j + 2) * (6 + NV) + r], ry[(j + 2) * (6 + NV) + 6 + a], s2);
-          s3 = fmaf(ry[(j + 3) * (6 + NV) + r], ry[(j + 3) * (6 + NV) + 6 + a], s3);
-        }
-        for (; j < S; ++j) s0 = fmaf(ry[j * (6 + NV) + r], ry[j * (6 + NV) + 6 + a], s0);
-        per[L::oDG + e] = -2.f * A.w_q * ((s0 + s1) + (s2 + s3));
-      }
-      if (lane == 0) {
-        float EQ = 0.f;
-        for (int j = 0; j < S; ++j) EQ += per[L::oQ + j];
-        float Ed = 0.f;
-        for (int i = 0; i < M; ++i) {
-          const float r = per[L::oCT + L::CTW * i + 9] - H.alpha - A.delta;
-          Ed = fmaf(r, r, Ed);
-        }
-        float Ec = 0.f;
-        if (A.coll)
-          for (int l = 0; l < S; ++l) Ec += per[L::oGC + MAXD + l];
-        sc[0] = A.w_q * EQ + A.w_d * Ed + Ec;
-      }
-    }
-    __syncthreads();
-    // ---- A7 (part 2): through the contact geometry and the kinematic chain
-    if (active && lane < M) {
-      const ContactGeo k = load_ct(per + L::oCT + L::CTW * lane);
-      float cols[18];
-      for (int r = 0; r < 6; ++r)
-        for (int cc = 0; cc < 3; ++cc) cols[r * 3 + cc] = per[L::oDG + r * NV + 3 * lane + cc];
-      float dEdc[3];
-      contact_adjoint(k, cols, 2.f * A.w_d * (k.phi - H.alpha - A.delta), dEdc);
-      const float* jw = per + L::oJW + lane * MAXCHAIN * 6;  // frames from the forward pass
-      const float* c = k.c;
-      float* cb = per + L::oCB + lane * (6 + MAXCHAIN);
-      cb[0] = dEdc[0];
-      cb[1] = dEdc[1];
-      cb[2] = dEdc[2];
-      // root rotations rx, ry, rz: axes through t
-      {
-        float s1, c1, s2, c2;
-        sincosf(xs[3], &s1, &c1);
-        sincosf(xs[4], &s2, &c2);
-        const float om[3][3] = {{1.f, 0.f, 0.f}, {0.f, c1, s1}, {s2, -s1 * c2, c1 * c2}};
-        const float rel[3] = {c[0] - xs[0], c[1] - xs[1], c[2] - xs[2]};
-        for (int k3 = 0; k3 < 3; ++k3) {
-          float v[3];
-          cross3(om[k3], rel, v);
-          cb[3 + k3] = dEdc[0] * v[0] + dEdc[1] * v[1] + dEdc[2] * v[2];
-        }
-      }
-      const int Lc = H.chain_len[lane];
-      for (int kk = 0; kk < Lc; ++kk) {
-        const float rel[3] = {c[0] - jw[6 * kk + 3], c[1] - jw[6 * kk + 4], c[2] - jw[6 * kk + 5]};
-        float v[3];
-        cross3(jw + 6 * kk, rel, v);
-        cb[6 + kk] = dEdc[0] * v[0] + dEdc[1] * v[1] + dEdc[2] * v[2];
-      }
-    }
-    __syncthreads();
-    // ---- gradient assembly (fixed order over contacts) and A8: Adam + clamp
-    if (active) {
-      const float* cb = per + L::oCB;
-      const int tstep = A.t0 + step + 1;
-      const float c1 = 1.f - powf(A.b1, (float)tstep), c2 = 1.f - powf(A.b2, (float)tstep);
-      for (int k = lane; k < D; k += S) {
-        float g = 0.f;
-        if (k < 6) {
-          for (int i = 0; i < M; ++i) g += cb[i * (6 + MAXCHAIN) + k];
-        } else {
-          for (int i = 0; i < M; ++i) {
-            const int pos = H.jpos[i][k - 6];
-            if (pos >= 0) g += cb[i * (6 + MAXCHAIN) + 6 + pos];
-          }
-        }
-        if (A.coll) g += per[L::oGC + k];
-        if (MODE != MODE_STEP) {
-          if (A.dEdx) A.dEdx[(size_t)b * D + k] = g;
-        } else {
-          const float mm = fmaf(A.b1, ams[k], (1.f - A.b1) * g);
-          const float vv = fmaf(A.b2, avs[k], (1.f - A.b2) * g * g);
-          ams[k] = mm;
-          avs[k] = vv;
-          const float lr = k < 3 ? A.lr_t : A.lr_r;
-          const float xn = xs[k] - lr * (mm / c1) / (sqrtf(vv / c2) + A.adam_eps);
-          xs[k] = fminf(fmaxf(xn, H.qmin[k]), H.qmax[k]);
-        }
-      }
-    }
-    __syncthreads();
-  }
-
-  // ---- write back
-  if (!active) return;
-  if (lane == 0) {
-    if (A.E) A.E[b] = sc[0];
-    if (A.status) A.status[b] = *stat;
-    if (A.res) A.res[b] = sc[2];
-  }
-  if (MODE == MODE_STEP) {
-    for (int k = lane; k < D; k += S) {
-      A.x_state[(size_t)b * D + k] = xs[k];
-      A.am[(size_t)b * D + k] = ams[k];
-      A.av[(size_t)b * D + k] = avs[k];
-    }
-  }
-  if (MODE == MODE_EVAL && A.qy) {
-#pragma unroll
-    for (int a = 0; a < NV; ++a) A.qy[a * NQ + q] = y[a];
-#pragma unroll
-    for (int r = 0; r < NC; ++r) A.qw[r * NQ + q] = w[r];
-  }
-  if (MODE == MODE_EVAL) {
-    if (A.Qout) A.Qout[q] = per[L::oQ + lane];
-    if (A.yout)
-#pragma unroll
-      for (int a = 0; a < NV; ++a) A.yout[q * NV + a] = y[a];
-  }
-}
-
-template <int M, int MODE, int CONE>
-__global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
-  extern __shared__ __align__(16) float smem[];
-  fused_cta<M, MODE, CONE>(A, blockIdx.x, A.gpb, smem);
-}
-
-// ============================================================================ kernel: several jobs in one launch
-// Jobs with different hand templates (m = 3, 4, 5), objects, batch sizes,
-// wrench sets and step counts share one launch: CTA c belongs to the job j
-// with cta_begin[j] <= c < cta_begin[j+1] and runs that job's fused step on
-// its tile of grasps.  The table travels in the kernel parameters, so a
-// launch needs no device memory of its own.
-struct MultiArgs {
-  int n_jobs;
-  int m[BODEX_MAX_JOBS];
-  int cta_begin[BODEX_MAX_JOBS + 1];
-  FusedArgs job[BODEX_MAX_JOBS];
-};
-
-static_assert(sizeof(MultiArgs) <= 32000, "job table must fit in the kernel parameter space");
-
-__global__ void __launch_bounds__(CTA_LANES, 4) multi_kernel(const __grid_constant__ MultiArgs A) {
-  extern __shared__ __align__(16) float smem[];
-  const int c = blockIdx.x;
-  int j = 0;
-  while (j + 1 < A.n_jobs && c >= A.cta_begin[j + 1]) ++j;
-  const FusedArgs& J = A.job[j];
-  const int cta = c - A.cta_begin[j];
-  switch (A.m[j]) {
-    case 3: fused_cta<3, MODE_STEP>(J, cta, J.gpb, smem); break;
-    case 4: fused_cta<4, MODE_STEP>(J, cta, J.gpb, smem); break;
-    default: fused_cta<5, MODE_STEP>(J, cta, J.gpb, smem); break;
-  }
 }
 
 // ============================================================================ kernel: refinement epilogue
@@ -875,50 +351,6 @@ __global__ void __launch_bounds__(RF_LANES * RF_GPB) metrics_kernel(MetricsArgs 
 // ============================================================================ host helpers
 namespace {
 
-// Grasps per CTA: 96 lanes / s, capped by the shared memory one CTA may use.
-template <int M>
-int gpb_for(int s) {
-  constexpr size_t kMaxSmem = 227 * 1024;
-  const size_t per = 4u * (size_t)(Lay<M>::KS + Lay<M>::PER);
-  const size_t fit = (kMaxSmem - 4u * Lay<M>::HAND_WORDS) / per;
-  return std::max(1, std::min(CTA_LANES / s, (int)fit));
-}
-
-// Grasps per CTA: the requested count (autotuner), else the default,
-// never more than fit in 96 lanes and in shared memory.
-template <int M>
-int pick_gpb(int s, int requested) {
-  const int cap = gpb_for<M>(s);
-  return requested > 0 ? std::min(requested, cap) : cap;
-}
-
-// Raises the kernel's dynamic shared-memory limit when needed, once per
-// device and size (so that launches recorded into a CUDA graph issue no
-// attribute calls after the first).
-template <class K>
-int ensure_smem(K kernel, size_t bytes) {
-  // A launch reports errors through cudaGetLastError; clear what an earlier,
-  // already reported failure may have left behind (sticky device faults are
-  // returned again by the next call regardless).
-  (void)cudaGetLastError();
-  if (bytes <= 48 * 1024) return BODEX_OK;
-  static std::mutex mu;
-  static std::map<std::pair<const void*, int>, size_t> configured;  // (kernel, device) -> bytes
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
-  const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), dev);
-  std::lock_guard<std::mutex> lock(mu);
-  auto it = configured.find(key);
-  if (it != configured.end() && it->second >= bytes) return BODEX_OK;
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e != cudaSuccess) {
-    (void)cudaGetLastError();
-    return cuda_fail(e, "cudaFuncSetAttribute");
-  }
-  configured[key] = bytes;
-  return BODEX_OK;
-}
-
 int check_qp_params(const bodex_qp_params* p, int m) {
   if (!p) return fail(BODEX_ERR_INVALID, "null qp params");
   if (!(p->gamma >= 0.f) || p->gamma > (float)m)
@@ -931,65 +363,13 @@ int check_qp_params(const bodex_qp_params* p, int m) {
   return BODEX_OK;
 }
 
-int launch_err(const char* what) {
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, what);
-  return BODEX_OK;
-}
-
-template <int M>
-int run_fused(int mode, const FusedArgs& A0, cudaStream_t st) {
-  FusedArgs A = A0;
-  A.gpb = pick_gpb<M>(A.S, A0.gpb);
-  const int gpb = A.gpb;
-  const size_t bytes = Lay<M>::bytes(gpb);
-  const dim3 grid((A.B + gpb - 1) / gpb), block(gpb * A.S);
-  if (A.B == 0) return BODEX_OK;
-  const bool soc = A.cfg.cone != 0;
-  if (mode == MODE_STEP && soc) {
-    if (int r = ensure_smem(fused_kernel<M, MODE_STEP, CONE_SOC>, bytes)) return r;
-    fused_kernel<M, MODE_STEP, CONE_SOC><<<grid, block, bytes, st>>>(A);
-  } else if (mode == MODE_STEP) {
-    if (int r = ensure_smem(fused_kernel<M, MODE_STEP, CONE_PYR>, bytes)) return r;
-    fused_kernel<M, MODE_STEP, CONE_PYR><<<grid, block, bytes, st>>>(A);
-  } else if (mode == MODE_ADJOINT) {  // no lower-level solve
-    if (int r = ensure_smem(fused_kernel<M, MODE_ADJOINT, CONE_PYR>, bytes)) return r;
-    fused_kernel<M, MODE_ADJOINT, CONE_PYR><<<grid, block, bytes, st>>>(A);
-  } else if (soc) {
-    if (int r = ensure_smem(fused_kernel<M, MODE_EVAL, CONE_SOC>, bytes)) return r;
-    fused_kernel<M, MODE_EVAL, CONE_SOC><<<grid, block, bytes, st>>>(A);
-  } else {
-    if (int r = ensure_smem(fused_kernel<M, MODE_EVAL, CONE_PYR>, bytes)) return r;
-    fused_kernel<M, MODE_EVAL, CONE_PYR><<<grid, block, bytes, st>>>(A);
-  }
-  return launch_err("fused_kernel launch");
-}
-
 int dispatch_fused(int m, int mode, const FusedArgs& A, cudaStream_t st) {
   switch (m) {
-    case 3: return run_fused<3>(mode, A, st);
-    case 4: return run_fused<4>(mode, A, st);
-    case 5: return run_fused<5>(mode, A, st);
+    case 3: return launch_fused_m3(mode, A, st);
+    case 4: return launch_fused_m4(mode, A, st);
+    case 5: return launch_fused_m5(mode, A, st);
     default: return fail(BODEX_ERR_INVALID, "m must be 3, 4 or 5");
   }
-}
-
-template <int M>
-int run_qp(const float* G, int B, const float* T, int s, const AdmmCfg& cfg, int warm, float* y, float* z,
-           float* lam, float* Q, int32_t* iters, int32_t* status, float* res, cudaStream_t st) {
-  if (B == 0) return BODEX_OK;
-  const int gpb = gpb_for<M>(s);
-  const size_t bytes = Lay<M>::bytes(gpb);
-  if (cfg.cone) {
-    if (int r = ensure_smem(qp_solve_kernel<M, CONE_SOC>, bytes)) return r;
-    qp_solve_kernel<M, CONE_SOC><<<(B + gpb - 1) / gpb, gpb * s, bytes, st>>>(G, B, T, s, cfg, warm, y, z, lam, Q,
-                                                                              iters, status, res);
-  } else {
-    if (int r = ensure_smem(qp_solve_kernel<M, CONE_PYR>, bytes)) return r;
-    qp_solve_kernel<M, CONE_PYR><<<(B + gpb - 1) / gpb, gpb * s, bytes, st>>>(G, B, T, s, cfg, warm, y, z, lam, Q,
-                                                                              iters, status, res);
-  }
-  return launch_err("qp_solve_kernel launch");
 }
 
 template <int M>
@@ -1354,13 +734,8 @@ int bodex_qp_solve_batch(const float* G, int B, int m, const float* T, int s, co
   AdmmCfg cfg = admm_cfg(*params);
   cfg.fp64_setup = params->eps_abs > 0.f ? 1 : 0;  // one setup per call: exact inverse is cheap
   cudaStream_t st = as_stream(stream);
-  int r;
-  switch (m) {
-    case 3: r = run_qp<3>(G, B, T, s, cfg, params->warm, y, z, lam, Q, iters, status, res, st); break;
-    case 4: r = run_qp<4>(G, B, T, s, cfg, params->warm, y, z, lam, Q, iters, status, res, st); break;
-    case 5: r = run_qp<5>(G, B, T, s, cfg, params->warm, y, z, lam, Q, iters, status, res, st); break;
-    default: return fail(BODEX_ERR_INVALID, "m must be 3, 4 or 5");
-  }
+  if (m < 3 || m > 5) return fail(BODEX_ERR_INVALID, "m must be 3, 4 or 5");
+  const int r = launch_qp(m, G, B, T, s, cfg, params->warm, y, z, lam, Q, iters, status, res, st);
   if (r || !params->strict || B == 0) return r;
   std::vector<int32_t> hs((size_t)B * s);
   BODEX_CUDA(cudaMemcpyAsync(hs.data(), status, hs.size() * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -1592,11 +967,8 @@ int bodex_step_multi(const bodex_job* jobs, int n_jobs, const bodex_step_params*
   MA->cta_begin[nj] = total;
   int r = BODEX_OK;
   if (nj > 0) {
-    r = ensure_smem(multi_kernel, bytes);
-    if (r == BODEX_OK) {
-      multi_kernel<<<total, CTA_LANES, bytes, as_stream(stream)>>>(*MA);
-      r = launch_err("multi_kernel launch");
-    }
+    const bool adapt = params->qp.eps_abs > 0.f && params->qp.adaptive_rho;
+    r = launch_multi(adapt, *MA, total, bytes, as_stream(stream));
     if (r == BODEX_OK)
       for (int k = 0; k < nj; ++k) jobs[take[k]].state->t += jobs[take[k]].n_steps;
   }

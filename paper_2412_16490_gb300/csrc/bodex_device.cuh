@@ -73,6 +73,7 @@ struct AdmmCfg {
   float mu_c8;  // mu cos(pi/8)
   float mu;
   int cone;     // 0: the 8-facet pyramid, 1: the elliptic cone
+  int adapt;    // adapt rho per grasp in solves with a residual target
   float beta, gamma, rho, sigma, alpha, eps, eps_reg;
   int iters, check;
   int fp64_setup;  // build K^-1 in double (set by the host per launch)
@@ -83,6 +84,7 @@ __host__ __device__ inline AdmmCfg admm_cfg(const bodex_qp_params& p) {
   c.mu_c8 = p.mu * C8;
   c.mu = p.mu;
   c.cone = p.cone;
+  c.adapt = p.adaptive_rho;
   c.beta = p.beta;
   c.gamma = p.gamma;
   c.rho = p.rho;
@@ -415,15 +417,24 @@ struct DiagK {
 };
 __device__ __forceinline__ DiagK diag_k(const AdmmCfg& c) {
   DiagK d;
+  const float base = fmaf(2.f, c.eps_reg, c.sigma);
   if (c.cone) {  // rows f_n and (mu f_n, f_d, f_e): A^T A = diag(1 + mu^2, 1, 1)
-    d.dn = c.sigma + 2.f * c.eps_reg + c.rho * (1.f + c.mu * c.mu);
-    d.dt = c.sigma + 2.f * c.eps_reg + c.rho;
+    d.dn = fmaf(c.rho, fmaf(c.mu, c.mu, 1.f), base);
+    d.dt = base + c.rho;
   } else {
-    d.dn = c.sigma + 2.f * c.eps_reg + c.rho * (1.f + 8.f * c.mu_c8 * c.mu_c8);
-    d.dt = c.sigma + 2.f * c.eps_reg + 4.f * c.rho;
+    d.dn = fmaf(c.rho, fmaf(8.f * c.mu_c8, c.mu_c8, 1.f), base);
+    d.dt = fmaf(4.f, c.rho, base);
   }
   return d;
 }
+
+// Fused multiply-add in float or double.  The QP setup, the ADMM iteration
+// and its residuals spell every multiply-add out (fmaf / fma_r) and leave no
+// `a * b + c` to the compiler's contraction, whose choice can depend on the
+// code a function is inlined into: kernels that inline the same solve in
+// different contexts then give bitwise equal results.
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
 
 // Entry e (0..27, row-major upper triangle of the 7x7) of M = I + V^T Dg^-1 V,
 // accumulated in precision R.
@@ -441,15 +452,14 @@ __device__ inline R woodbury_M_entry(const float* G, int e, const AdmmCfg& c, co
   const R idn = R(1) / R(dk.dn), idt = R(1) / R(dk.dt);
   R s = 0;
   if (b < 6) {  // both columns from sqrt2 G^T
-    for (int i = 0; i < NV; ++i) s += R(G[a * NV + i]) * R(G[b * NV + i]) * ((i % 3 == 0) ? idn : idt);
-    s *= R(2);
-  } else if (a < 6) {  // sqrt2 G^T against sqrt(rho) u
-    for (int i = 0; i < NV; i += 3) s += R(G[a * NV + i]);
-    s *= sqrt(R(2) * R(c.rho)) * idn;
-  } else {
-    s = R(c.rho) * R(M) * idn;
+    for (int i = 0; i < NV; ++i) s = fma_r(R(G[a * NV + i]) * R(G[b * NV + i]), (i % 3 == 0) ? idn : idt, s);
+    return fma_r(R(2), s, a == b ? R(1) : R(0));
   }
-  return (a == b ? R(1) : R(0)) + s;
+  if (a < 6) {  // sqrt2 G^T against sqrt(rho) u
+    for (int i = 0; i < NV; i += 3) s += R(G[a * NV + i]);
+    return s * (sqrt(R(2) * R(c.rho)) * idn);
+  }
+  return fma_r(R(c.rho) * R(M), idn, R(1));
 }
 
 // Scratch (in floats) that setup_kinv_woodbury<M, R> needs.
@@ -487,7 +497,7 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
     for (int j = 0; j < 7; ++j) {
       R d = L[idx(j, j)];
 #pragma unroll
-      for (int k = 0; k < j; ++k) d -= L[idx(k, j)] * L[idx(k, j)];
+      for (int k = 0; k < j; ++k) d = fma_r(-L[idx(k, j)], L[idx(k, j)], d);
       const R ljj = sqrt(d > R(1e-30) ? d : R(1e-30));
       L[idx(j, j)] = ljj;
       const R il = R(1) / ljj;
@@ -495,7 +505,7 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
       for (int i = j + 1; i < 7; ++i) {
         R t = L[idx(j, i)];
 #pragma unroll
-        for (int k = 0; k < j; ++k) t -= L[idx(k, i)] * L[idx(k, j)];
+        for (int k = 0; k < j; ++k) t = fma_r(-L[idx(k, i)], L[idx(k, j)], t);
         L[idx(j, i)] = t * il;
       }
     }
@@ -514,7 +524,7 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
       for (int a = 0; a < 7; ++a) {
         R t = w[a];
 #pragma unroll
-        for (int k = 0; k < a; ++k) t -= L[idx(k, a)] * w[k];
+        for (int k = 0; k < a; ++k) t = fma_r(-L[idx(k, a)], w[k], t);
         w[a] = t * ild[a];
       }
 #pragma unroll
@@ -531,7 +541,7 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
       for (int j = i; j < NV; ++j) {
         R t = 0;
 #pragma unroll
-        for (int a = 0; a < 7; ++a) t += ui[a] * Us[j * 8 + a];
+        for (int a = 0; a < 7; ++a) t = fma_r(ui[a], Us[j * 8 + a], t);
         Kinv[Admm<M>::tri(i, j)] = (float)(R(c.alpha) * ((i == j ? id : R(0)) - t));
       }
     }
@@ -578,8 +588,8 @@ __device__ __forceinline__ void At_contact(float v0, const float (&vk)[8], float
                                            float& ge) {
   const float sum = ((vk[0] + vk[1]) + (vk[2] + vk[3])) + ((vk[4] + vk[5]) + (vk[6] + vk[7]));
   gn = fmaf(-mu_c8, sum, v0);
-  gd = C8 * ((vk[0] + vk[7]) - (vk[3] + vk[4])) + S8 * ((vk[1] + vk[6]) - (vk[2] + vk[5]));
-  ge = S8 * ((vk[0] + vk[3]) - (vk[4] + vk[7])) + C8 * ((vk[1] + vk[2]) - (vk[5] + vk[6]));
+  gd = fmaf(C8, (vk[0] + vk[7]) - (vk[3] + vk[4]), S8 * ((vk[1] + vk[6]) - (vk[2] + vk[5])));
+  ge = fmaf(S8, (vk[0] + vk[3]) - (vk[4] + vk[7]), C8 * ((vk[1] + vk[2]) - (vk[5] + vk[6])));
 }
 
 template <int M>
@@ -588,10 +598,10 @@ __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* 
   constexpr int NV = Admm<M>::NV;
   // rhs = sigma y - q + rho A^T v,  v = 2 Pi(w) - w, one contact at a time
   float rhs[NV];
-  const float vsum = 2.f * fmaxf(w[9 * M], c.gamma) - w[9 * M];
+  const float vsum = fmaf(2.f, fmaxf(w[9 * M], c.gamma), -w[9 * M]);
 #pragma unroll
   for (int i = 0; i < M; ++i) {
-    const float v0 = 2.f * fminf(fmaxf(w[9 * i], 0.f), 1.f) - w[9 * i] + vsum;
+    const float v0 = fmaf(2.f, fminf(fmaxf(w[9 * i], 0.f), 1.f), -w[9 * i]) + vsum;
     // facet rows (bounds (-inf, 0]): 2 min(w, 0) - w is exactly -|w|, which
     // the hardware applies as a free operand modifier
     float vk[8];
@@ -675,7 +685,7 @@ __device__ inline void admm_residuals(const float* y, const float* w, const floa
   rd = 0.f;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
-    const float l0 = c.rho * (w[9 * i] - fminf(fmaxf(w[9 * i], 0.f), 1.f)) + lsum;
+    const float l0 = fmaf(c.rho, w[9 * i] - fminf(fmaxf(w[9 * i], 0.f), 1.f), lsum);
     float lk[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) lk[k] = c.rho * (w[9 * i + 1 + k] - fminf(w[9 * i + 1 + k], 0.f));
@@ -687,7 +697,7 @@ __device__ inline void admm_residuals(const float* y, const float* w, const floa
       float s = 0.f;
 #pragma unroll
       for (int r = 0; r < 6; ++r) s = fmaf(lds32(G + r * NV + a), gy[r], s);
-      const float py = 2.f * s + 2.f * c.eps_reg * y[a];
+      const float py = fmaf(2.f * c.eps_reg, y[a], 2.f * s);
       rd = fmaxf(rd, fabsf(py - mq[a] + at[q]));
     }
   }
@@ -717,7 +727,7 @@ constexpr int CONE_PYR = 0, CONE_SOC = 1;
 // Euclidean projection onto the second-order cone {|(u1, u2)| <= s}
 // (e.g. Parikh & Boyd, Proximal Algorithms, Sec. 6.3.2).
 __device__ __forceinline__ void proj_soc(float s, float u1, float u2, float& ps, float& p1, float& p2) {
-  const float nu = sqrtf(u1 * u1 + u2 * u2);
+  const float nu = sqrtf(fmaf(u1, u1, u2 * u2));
   if (nu <= s) {
     ps = s;
     p1 = u1;
@@ -738,7 +748,7 @@ __device__ __forceinline__ void admm_iteration_soc(float* y, float* w, const flo
   constexpr int NV = Admm<M>::NV;
   // rhs = sigma y - q + rho A^T (2 Pi(w) - w), keeping Pi of the cone rows
   float rhs[NV], pc[3 * M];
-  const float vsum = 2.f * fmaxf(w[4 * M], c.gamma) - w[4 * M];
+  const float vsum = fmaf(2.f, fmaxf(w[4 * M], c.gamma), -w[4 * M]);
 #pragma unroll
   for (int i = 0; i < M; ++i) {
     const float* wi = w + 4 * i;
@@ -797,7 +807,7 @@ __device__ inline void admm_residuals_soc(const float* y, const float* w, const 
     float ps, p1, p2;
     proj_soc(wi[1], wi[2], wi[3], ps, p1, p2);
     rp = fmaxf(rp, fabsf(yn - p0));
-    rp = fmaxf(rp, fabsf(c.mu * yn - ps));
+    rp = fmaxf(rp, fabsf(fmaf(c.mu, yn, -ps)));
     rp = fmaxf(rp, fabsf(yd - p1));
     rp = fmaxf(rp, fabsf(ye - p2));
     lam[4 * i] = c.rho * (wi[0] - p0);
@@ -818,14 +828,14 @@ __device__ inline void admm_residuals_soc(const float* y, const float* w, const 
   rd = 0.f;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
-    const float at[3] = {lam[4 * i] + c.mu * lam[4 * i + 1] + lsum, lam[4 * i + 2], lam[4 * i + 3]};
+    const float at[3] = {fmaf(c.mu, lam[4 * i + 1], lam[4 * i]) + lsum, lam[4 * i + 2], lam[4 * i + 3]};
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
       const int a = 3 * i + q;
       float s = 0.f;
 #pragma unroll
       for (int r = 0; r < 6; ++r) s = fmaf(lds32(G + r * NV + a), gy[r], s);
-      const float py = 2.f * s + 2.f * c.eps_reg * y[a];
+      const float py = fmaf(2.f * c.eps_reg, y[a], 2.f * s);
       rd = fmaxf(rd, fabsf(py - mq[a] + at[q]));
     }
   }
@@ -878,6 +888,94 @@ __device__ inline int admm_solve(float* y, float* w, const float* mq, const floa
 #pragma unroll 1
     for (; it < c.iters; ++it) iterate();
     residuals();
+  }
+  return it;
+}
+
+// Re-expresses the iterate for a new penalty rho' (ratio = rho / rho'),
+// keeping z = Pi(w) and lam = rho (w - Pi(w)): w <- Pi(w) + ratio (w - Pi(w)).
+template <int M, int CONE>
+__device__ inline void rescale_w(float* w, float ratio, const AdmmCfg& c) {
+  if (CONE == CONE_SOC) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      float* wi = w + 4 * i;
+      const float p0 = __saturatef(wi[0]);
+      wi[0] = fmaf(ratio, wi[0] - p0, p0);
+      float ps, p1, p2;
+      proj_soc(wi[1], wi[2], wi[3], ps, p1, p2);
+      wi[1] = fmaf(ratio, wi[1] - ps, ps);
+      wi[2] = fmaf(ratio, wi[2] - p1, p1);
+      wi[3] = fmaf(ratio, wi[3] - p2, p2);
+    }
+    const float ps = fmaxf(w[4 * M], c.gamma);
+    w[4 * M] = fmaf(ratio, w[4 * M] - ps, ps);
+  } else {
+#pragma unroll
+    for (int r = 0; r < 9 * M + 1; ++r) {
+      const float p = proj_row<M>(w[r], r, c.gamma);
+      w[r] = fmaf(ratio, w[r] - p, p);
+    }
+  }
+}
+
+// ADMM to a residual target with the penalty adapted per grasp (the
+// residual-balancing rule of OSQP, Stellato et al. 2020, Sec. 5.2):
+// every `check` iterations each lane still running proposes
+// rho * sqrt(r_p / r_d); when the geometric mean of its grasp's proposals
+// moves rho by more than 5x, the grasp re-expresses its iterates and rebuilds
+// K^-1 (all of its lanes share one K).  Lanes that converged stop iterating
+// but keep their grasp's rho.  Must be called by every thread of the CTA
+// (barriers); `active` marks the threads that own a QP, `vote` is S floats
+// of shared memory per grasp, `scratch` the K^-1 setup scratch.  c.rho is
+// this lane's (its grasp's) current penalty on return.
+template <int M, int CONE, typename SetupFn>
+__device__ inline int admm_solve_adaptive(bool active, int lane, int S, float* y, float* w, const float* mq,
+                                          const float* Kinv, const float* G, AdmmCfg& c, float* vote,
+                                          SetupFn&& setup, float& rp, float& rd, bool& conv) {
+  int it = 0;
+  conv = !active;
+  rp = rd = 0.f;
+  const float tol = 1.6094379f;  // log 5
+#pragma unroll 1
+  for (;;) {
+    if (!conv && it < c.iters) {
+      const int chunk = min(c.check, c.iters - it);
+#pragma unroll 1
+      for (int k = 0; k < chunk; ++k) {
+        if (CONE == CONE_SOC) admm_iteration_soc<M>(y, w, mq, Kinv, c);
+        else admm_iteration<M>(y, w, mq, Kinv, c);
+      }
+      it += chunk;
+      if (CONE == CONE_SOC) admm_residuals_soc<M>(y, w, mq, G, c, rp, rd);
+      else admm_residuals<M>(y, w, mq, G, c, rp, rd);
+      conv = rp <= c.eps && rd <= c.eps;
+    }
+    const bool done = conv || it >= c.iters;
+    if (__syncthreads_and(done)) break;
+    if (active) vote[lane] = done ? 0.f : 0.5f * __logf(fmaxf(rp, 1e-12f) / fmaxf(rd, 1e-12f));
+    __syncthreads();
+    // every lane of a grasp reads the same votes in the same order: one decision per grasp
+    float sh = 0.f;
+    int cnt = 0;
+    if (active)
+      for (int j = 0; j < S; ++j) {
+        const float v = vote[j];
+        sh += v;
+        cnt += v != 0.f;
+      }
+    bool upd = active && cnt > 0 && fabsf(sh / cnt) > tol;
+    float rho_new = c.rho;
+    if (upd) {
+      rho_new = fminf(fmaxf(c.rho * __expf(sh / cnt), 1e-6f), 1e6f);
+      upd = rho_new != c.rho;
+    }
+    __syncthreads();  // votes read before the next round writes them
+    if (upd) {
+      rescale_w<M, CONE>(w, c.rho / rho_new, c);
+      c.rho = rho_new;
+    }
+    setup(upd, c);  // rebuilds K^-1 of the grasps that changed (contains barriers)
   }
   return it;
 }
@@ -990,7 +1088,7 @@ __device__ __forceinline__ float penetration_hinge(float p, float eta, float& dh
 // The argument structs are copied into registers first: through references
 // every use would be a local-memory load that stores to shared memory force
 // the compiler to repeat.
-__device__ __noinline__ void collision_phase(bool active, int lane, int S, const HandDev& H, const CollDev& Cr,
+static __device__ __noinline__ void collision_phase(bool active, int lane, int S, const HandDev& H, const CollDev& Cr,
                                              const ObjDev& Or, const float* x, const CollParams& Pr,
                                              const float* frames, const float* jw, float* cs, float* sl, float* bw,
                                              float* gc, float* ep) {

@@ -1,0 +1,735 @@
+// Kernels and launch helpers shared by the library's translation units:
+// the per-grasp shared-memory layout, the batched-QP kernel, the fused
+// step kernel and the several-job kernel.  bodex.cu holds the C ABI and the
+// small kernels; qp.cu, fused_m3.cu, fused_m4.cu, fused_m5.cu and
+// fused_multi.cu instantiate the heavy kernels, so that nvcc compiles them
+// in parallel.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstddef>
+#include <map>
+#include <mutex>
+#include <string>
+
+#include "../../include/bodex.h"
+#include "bodex_device.cuh"
+
+namespace bodex {
+// error state of the C ABI (bodex.cu)
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* where);
+int launch_err(const char* what);
+}  // namespace bodex
+
+using namespace bodex;
+
+// ============================================================================ shared-memory layout
+constexpr int CTA_LANES = 96;
+
+__host__ __device__ constexpr int align4(int v) { return (v + 3) & ~3; }
+
+template <int M>
+struct Lay {
+  static constexpr int NV = 3 * M, NC = 9 * M + 1, NVP = (NV + 3) & ~3;
+  // K^-1 block per grasp (packed upper triangle in whole float4s); the
+  // stride is skewed (== 20 mod 32 words) so that lanes of two or three
+  // grasps in one warp hit disjoint banks.
+  static constexpr int KT = 4 * Admm<M>::NTRI4;
+  static constexpr int KS = KT + ((20 - KT % 32) + 32) % 32;
+  static constexpr int CTW = 24;  // floats per contact record
+  static constexpr int oG = 0;
+  static constexpr int oK = oG + 6 * NV;  // K^-1 setup scratch
+  static constexpr int oCT = oK + WoodburyScratch<M, double>::floats;
+  static constexpr int oRY = oCT + CTW * M;
+  static constexpr int oQ = oRY + SMAX * (6 + NV);
+  static constexpr int oDG = oQ + SMAX;
+  static constexpr int oCB = oDG + 6 * NV;
+  static constexpr int oX = oCB + M * (6 + MAXCHAIN);
+  static constexpr int oAM = oX + MAXD;
+  static constexpr int oAV = oAM + MAXD;
+  static constexpr int oJW = oAV + MAXD;  // chain joint axes/points, M x MAXCHAIN x 6
+  static constexpr int oGC = oJW + M * MAXCHAIN * 6;  // collision gradient [MAXD], energy by lane [SMAX]
+  static constexpr int oSC = oGC + MAXD + SMAX;
+  // collision scratch: link frames in the K^-1 setup scratch, sphere centres
+  // and slot sums in the r / Q / dE/dG block (both dead before A4)
+  static constexpr int COLL_FR = WoodburyScratch<M, double>::floats;
+  static constexpr int COLL_CS = SMAX * (6 + NV) + SMAX + 6 * NV;
+  // per-grasp stride == 12 (mod 32) words: the two or three grasps that
+  // share a warp then map the same offset to different banks
+  static constexpr int PER = align4(oSC + 4) + ((12 - align4(oSC + 4) % 32) + 32) % 32;
+  static constexpr int HAND_WORDS = align4((int)(sizeof(HandDev) / 4));
+  static size_t bytes(int gpb) { return 4u * (size_t)(HAND_WORDS + gpb * (KS + PER)); }
+};
+
+// Contact record in shared memory: c(3) p(3) n(3) phi g(3) h(6) cell(3) degenerate.
+__device__ __forceinline__ void store_ct(float* r, const ContactGeo& k) {
+  for (int a = 0; a < 3; ++a) {
+    r[a] = k.c[a];
+    r[3 + a] = k.p[a];
+    r[6 + a] = k.n[a];
+    r[10 + a] = k.g[a];
+    r[19 + a] = __int_as_float(k.cell[a]);
+  }
+  r[9] = k.phi;
+  for (int e = 0; e < 6; ++e) r[13 + e] = k.h[e];
+  r[22] = __int_as_float(k.degenerate);
+}
+__device__ __forceinline__ ContactGeo load_ct(const float* r) {
+  ContactGeo k;
+  for (int a = 0; a < 3; ++a) {
+    k.c[a] = r[a];
+    k.p[a] = r[3 + a];
+    k.n[a] = r[6 + a];
+    k.g[a] = r[10 + a];
+    k.cell[a] = __float_as_int(r[19 + a]);
+  }
+  k.phi = r[9];
+  for (int e = 0; e < 6; ++e) k.h[e] = r[13 + e];
+  k.degenerate = __float_as_int(r[22]);
+  return k;
+}
+
+__device__ __forceinline__ void copy_hand_to_smem(const HandDev* src, float* dst) {
+  const int* s = reinterpret_cast<const int*>(src);
+  int* d = reinterpret_cast<int*>(dst);
+  const int words = (int)(sizeof(HandDev) / 4);
+  for (int i = threadIdx.x; i < words; i += blockDim.x) d[i] = __ldg(s + i);
+}
+
+__device__ __forceinline__ bool finite3(const float* v) {
+  return isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]);
+}
+
+// ============================================================================ per-grasp QP setup (shared by kernels)
+// K^-1 of every grasp of the CTA (Woodbury form, all lanes); must be called
+// by every thread of the CTA (contains barriers).
+// Double precision when the host asks for it (solves that iterate to a
+// tight residual target), single precision otherwise; the branch is
+// uniform per launch.
+template <int M>
+__device__ inline void setup_kinv(bool active, int lane, int S, const float* Gs, float* scratch, float* Kinv,
+                                  const AdmmCfg& cfg) {
+  if (cfg.fp64_setup) setup_kinv_woodbury<M, double>(active, lane, S, Gs, scratch, Kinv, cfg);
+  else setup_kinv_woodbury<M, float>(active, lane, S, Gs, scratch, Kinv, cfg);
+}
+
+// ============================================================================ kernel: batched QP
+template <int M, int CONE>
+__global__ void __launch_bounds__(CTA_LANES) qp_solve_kernel(const float* __restrict__ Gin, int B,
+                                                             const float* __restrict__ T, int S, AdmmCfg cfg,
+                                                             int warm, float* yio, float* zio, float* lio,
+                                                             float* Qout, int32_t* iters_out, int32_t* status_out,
+                                                             float* res_out) {
+  using L = Lay<M>;
+  constexpr int NV = L::NV, NC = CONE == CONE_SOC ? 4 * M + 1 : L::NC;  // ADMM rows
+  extern __shared__ __align__(16) float smem[];
+  const int GPB = blockDim.x / S;
+  const int gl = threadIdx.x / S, lane = threadIdx.x % S;
+  const int b = blockIdx.x * GPB + gl;
+  const bool active = (gl < GPB) && (b < B);
+  float* kin = smem + L::HAND_WORDS + gl * L::KS;
+  float* per = smem + L::HAND_WORDS + GPB * L::KS + gl * L::PER;
+  float* Gs = per + L::oG;
+  int* stat = reinterpret_cast<int*>(per + L::oSC + 1);
+  if (active) {
+    for (int e = lane; e < 6 * NV; e += S) Gs[e] = Gin[(size_t)b * 6 * NV + e];
+    if (lane == 0) *stat = 0;
+  }
+  __syncthreads();
+  setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg);
+  // solves with a residual target adapt rho per grasp, which needs every
+  // thread at the barriers; otherwise idle threads leave here
+  const bool adaptive = cfg.eps > 0.f && cfg.adapt;  // uniform
+  if (!active && !adaptive) return;
+  const size_t q = (size_t)b * S + lane;
+  float y[NV], w[NC], mq[NV];
+  float t[6];
+  if (active) {
+    for (int r = 0; r < 6; ++r) t[r] = T[lane * 6 + r];
+    neg_q<M>(Gs, t, cfg.beta, mq);
+  }
+  if (!active) {
+  } else if (warm) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) y[a] = yio[q * NV + a];
+#pragma unroll
+    for (int r = 0; r < NC; ++r) w[r] = zio[q * NC + r] + lio[q * NC + r] / cfg.rho;
+  } else {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) y[a] = 0.f;
+#pragma unroll
+    for (int r = 0; r < NC; ++r) w[r] = 0.f;
+  }
+  float rp, rd;
+  bool conv;
+  AdmmCfg cl = cfg;  // this grasp's penalty may move
+  int it;
+  if (adaptive) {
+    auto setup = [&](bool upd, const AdmmCfg& cc) { setup_kinv<M>(upd, lane, S, Gs, per + L::oK, kin, cc); };
+    it = admm_solve_adaptive<M, CONE>(active, lane, S, y, w, mq, kin, Gs, cl, per + L::oQ, setup, rp, rd, conv);
+    if (!active) return;  // no barriers below
+  } else {
+    it = admm_solve<M, CONE>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
+  }
+  float Q = 0.f;
+  bool fin = true;
+#pragma unroll
+  for (int r = 0; r < 6; ++r) {
+    float s = cfg.beta * t[r];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) s = fmaf(-Gs[r * NV + a], y[a], s);
+    Q = fmaf(s, s, Q);
+  }
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    yio[q * NV + a] = y[a];
+    fin = fin && isfinite(y[a]);
+    Q = fmaf(cfg.eps_reg * y[a], y[a], Q);  // regularised value when eps_reg > 0
+  }
+#pragma unroll
+  for (int r = 0; r < NC; ++r) {
+    const float p = CONE == CONE_SOC ? proj_row_soc<M>(w, r, cfg.gamma) : proj_row<M>(w[r], r, cfg.gamma);
+    zio[q * NC + r] = p;
+    lio[q * NC + r] = cl.rho * (w[r] - p);
+  }
+  Qout[q] = Q;
+  if (iters_out) iters_out[q] = it;
+  if (res_out) {
+    res_out[2 * q] = rp;
+    res_out[2 * q + 1] = rd;
+  }
+  int st = *stat;
+  if (!fin || !isfinite(Q)) st |= BODEX_ST_NONFINITE;
+  if (cfg.eps > 0.f && !conv) st |= BODEX_ST_NOT_CONVERGED;
+  if (status_out) status_out[q] = st;
+}
+
+// ============================================================================ kernel: fused evaluation / step
+struct FusedArgs {
+  const HandDev* hand;
+  ObjDev obj;
+  const float* T;
+  int S, B;
+  AdmmCfg cfg;
+  float w_q, w_d, delta;
+  float lr_t, lr_r, b1, b2, adam_eps;
+  int n_steps, t0;
+  // pose input (eval) or state pose (step), updated in place for step
+  const float* x_in;
+  float* x_state;
+  float* am;
+  float* av;
+  float* qy;  // warm start: may be null in eval (cold start); the state's arrays in step mode
+  float* qw;
+  // outputs
+  float* E;
+  float* dEdx;
+  float* Qout;
+  float* yout;
+  int32_t* status;
+  const float* yin;  // MODE_ADJOINT: forces from a previous solve [B, s, 3m]
+  float* res;        // [B] max ADMM residual of the grasp's QPs at the last step (may be null)
+  int gpb;           // grasps per CTA
+  int dfc;           // 1: the DFC force-closure energy |G u|^2 replaces the QPs (uniform per launch)
+  int coll;          // 1: the collision energies are on (uniform per launch)
+  CollDev cd;
+  CollParams cp;
+};
+
+// MODE_EVAL: E and dE/dx at x.  MODE_STEP: n_steps upper iterations on the
+// state.  MODE_ADJOINT: E and dE/dx at x for given forces y (no QP solve):
+// the backward pass of the energy, with FK and the SDF query recomputed.
+enum { MODE_EVAL = 0, MODE_STEP = 1, MODE_ADJOINT = 2 };
+
+// The work of one CTA: GPB grasps (cta * GPB ...) of one job, s lanes each;
+// threads beyond GPB * s idle but take part in every barrier.
+// CONE: CONE_PYR or CONE_SOC fixes the lower-level cone at compile time;
+// CONE_ANY reads it from the arguments (the several-job kernel).  ADAPT:
+// whether the kernel contains the adaptive-rho solve (residual-target
+// solves); kernels for fixed iteration counts leave it out, as its code
+// costs the fixed loop registers.
+constexpr int CONE_ANY = -1;
+
+template <int M, int MODE, int CONE = CONE_ANY, bool ADAPT = false>
+__device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, float* smem) {
+  using L = Lay<M>;
+  constexpr int NV = L::NV, NC = L::NC;
+  copy_hand_to_smem(A.hand, smem);
+  const int S = A.S;
+  const int gl = threadIdx.x / S, lane = threadIdx.x % S;
+  const int b = cta * GPB + gl;
+  const bool active = (gl < GPB) && (b < A.B);
+  const HandDev& H = *reinterpret_cast<const HandDev*>(smem);
+  float* kin = smem + L::HAND_WORDS + gl * L::KS;
+  float* per = smem + L::HAND_WORDS + GPB * L::KS + gl * L::PER;
+  float* Gs = per + L::oG;
+  float* xs = per + L::oX;
+  float* ams = per + L::oAM;
+  float* avs = per + L::oAV;
+  float* sc = per + L::oSC;
+  int* stat = reinterpret_cast<int*>(sc + 1);
+  __syncthreads();  // hand copied
+  const int D = H.D;
+  const AdmmCfg& cfg = A.cfg;
+
+  if (active) {
+    const float* xsrc = (MODE == MODE_STEP) ? A.x_state : A.x_in;
+    for (int k = lane; k < D; k += S) {
+      xs[k] = xsrc[(size_t)b * D + k];
+      if (MODE == MODE_STEP) {
+        ams[k] = A.am[(size_t)b * D + k];
+        avs[k] = A.av[(size_t)b * D + k];
+      }
+    }
+    if (lane == 0) {
+      *stat = 0;
+      sc[2] = 0.f;      // max residual of the grasp's QPs at the last step
+      sc[3] = cfg.rho;  // the grasp's ADMM penalty (adapted in solves with a residual target)
+    }
+  }
+  // ADMM iterate of this lane's QP.  In MODE_STEP it lives in the state's
+  // warm-start arrays between upper steps and in registers only around the
+  // solve, so the FK / SDF / adjoint phases get the registers it would hold.
+  float y[NV], w[NC];
+  const size_t q = (size_t)b * S + lane, NQ = (size_t)A.B * S;
+  if (MODE == MODE_ADJOINT && active) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) y[a] = A.yin[q * NV + a];
+#pragma unroll
+    for (int r = 0; r < NC; ++r) w[r] = 0.f;
+  } else if (MODE == MODE_EVAL && active && A.qy) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) y[a] = A.qy[a * NQ + q];
+#pragma unroll
+    for (int r = 0; r < NC; ++r) w[r] = A.qw[r * NQ + q];
+  } else {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) y[a] = 0.f;
+#pragma unroll
+    for (int r = 0; r < NC; ++r) w[r] = 0.f;
+  }
+  float t[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  if (active)
+    for (int r = 0; r < 6; ++r) t[r] = A.T[lane * 6 + r];
+  __syncthreads();
+
+  for (int step = 0; step < A.n_steps; ++step) {
+    // ---- A1-A3: kinematics, nearest-point query, grasp matrix (lane = contact)
+    if (active && lane < M) {
+      float c[3];
+      fk_contact(H, lane, xs, c, per + L::oJW + lane * MAXCHAIN * 6,
+                 (A.coll && A.cd.K > 0) ? per + L::oK : nullptr);  // link frames for the collision spheres
+      const ContactGeo k = contact_geometry(A.obj, c);
+      store_ct(per + L::oCT + L::CTW * lane, k);
+      write_G_block(k, lane, NV, Gs);
+      int st = 0;
+      if (k.degenerate) st |= BODEX_ST_DEGENERATE_NORMAL;
+      if (!finite3(k.p) || !finite3(k.n) || !isfinite(k.phi)) st |= BODEX_ST_NONFINITE;
+      if (st) atomicOr(stat, st);
+    }
+    __syncthreads();
+    // ---- constraint energies on the collision spheres (Sec. IV-B)
+    if (A.coll)
+      collision_phase(active, lane, S, H, A.cd, A.obj, xs, A.cp, per + L::oK, per + L::oJW, per + L::oRY,
+                      per + L::oRY + 3 * A.cd.K, per + L::oRY + 3 * A.cd.K + 6 * (H.n + 1), per + L::oGC,
+                      per + L::oGC + MAXD);
+    // ---- A4: K^-1 per grasp (at the grasp's current penalty)
+    if (MODE != MODE_ADJOINT && !A.dfc) {
+      if constexpr (ADAPT) {
+        AdmmCfg cg = cfg;
+        cg.rho = sc[3];
+        setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cg);
+      } else {
+        setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg);
+      }
+    }
+    // ---- A5: ADMM, one QP per lane
+    if (active && A.dfc) per[L::oQ + lane] = 0.f;  // no lower-level QPs under DFC
+    bool conv = true;
+    // r_j, Q_j, the stored iterate and the status of this lane's QP
+    auto finish_qp = [&]() {
+      float* ry = per + L::oRY + lane * (6 + NV);
+      float Q = 0.f;
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        float s = cfg.beta * t[r];
+#pragma unroll
+        for (int a = 0; a < NV; ++a) s = fmaf(-Gs[r * NV + a], y[a], s);
+        ry[r] = s;
+        Q = fmaf(s, s, Q);
+      }
+#pragma unroll
+      for (int a = 0; a < NV; ++a) {
+        ry[6 + a] = y[a];
+        Q = fmaf(cfg.eps_reg * y[a], y[a], Q);  // regularised value when eps_reg > 0
+      }
+      per[L::oQ + lane] = Q;
+      if (MODE == MODE_STEP) {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) A.qy[a * NQ + q] = y[a];
+#pragma unroll
+        for (int r = 0; r < NC; ++r) A.qw[r * NQ + q] = w[r];
+      }
+      int st = 0;
+      if (cfg.eps > 0.f && !conv) st |= BODEX_ST_NOT_CONVERGED;
+      if (!isfinite(Q)) st |= BODEX_ST_NONFINITE;
+      if (st) atomicOr(stat, st);
+    };
+    const bool soc = CONE == CONE_ANY ? cfg.cone != 0 : CONE == CONE_SOC;
+    if constexpr (ADAPT) {
+      // solves with a residual target adapt rho per grasp (every thread takes
+      // part); the iterate is stored with rho0 = cfg.rho and re-expressed at
+      // the grasp's rho here
+      if (!A.dfc) {
+        float mq[NV];
+        float rp = 0.f, rd = 0.f;
+        AdmmCfg cg = cfg;
+        cg.rho = sc[3];
+        if (active) {
+          if (MODE == MODE_STEP) {
+#pragma unroll
+            for (int a = 0; a < NV; ++a) y[a] = A.qy[a * NQ + q];
+#pragma unroll
+            for (int r = 0; r < NC; ++r) w[r] = A.qw[r * NQ + q];
+          }
+          if (MODE != MODE_ADJOINT) neg_q<M>(Gs, t, cfg.beta, mq);
+          if (cg.rho != cfg.rho) {
+            if (soc) rescale_w<M, CONE_SOC>(w, cfg.rho / cg.rho, cg);
+            else rescale_w<M, CONE_PYR>(w, cfg.rho / cg.rho, cg);
+          }
+        }
+        if (MODE != MODE_ADJOINT) {
+          auto setup = [&](bool upd, const AdmmCfg& cc) { setup_kinv<M>(upd, lane, S, Gs, per + L::oK, kin, cc); };
+          if (soc)
+            admm_solve_adaptive<M, CONE_SOC>(active, lane, S, y, w, mq, kin, Gs, cg, per + L::oQ, setup, rp, rd, conv);
+          else
+            admm_solve_adaptive<M, CONE_PYR>(active, lane, S, y, w, mq, kin, Gs, cg, per + L::oQ, setup, rp, rd, conv);
+          if (active) {
+            if (lane == 0) sc[3] = cg.rho;  // every lane of the grasp holds the same rho
+            if (cg.rho != cfg.rho) {
+              if (soc) rescale_w<M, CONE_SOC>(w, cg.rho / cfg.rho, cg);
+              else rescale_w<M, CONE_PYR>(w, cg.rho / cfg.rho, cg);
+            }
+            if (step == A.n_steps - 1) atomicMax(reinterpret_cast<int*>(sc + 2), __float_as_int(fmaxf(rp, rd)));
+          }
+        }
+        if (active) finish_qp();
+      }
+    } else if (active && !A.dfc) {
+      if (MODE == MODE_STEP) {
+#pragma unroll
+        for (int a = 0; a < NV; ++a) y[a] = A.qy[a * NQ + q];
+#pragma unroll
+        for (int r = 0; r < NC; ++r) w[r] = A.qw[r * NQ + q];
+      }
+      if (MODE != MODE_ADJOINT) {
+        float mq[NV];
+        neg_q<M>(Gs, t, cfg.beta, mq);
+        float rp, rd;
+        if (soc) admm_solve<M, CONE_SOC>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
+        else admm_solve<M, CONE_PYR>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
+        if (step == A.n_steps - 1) atomicMax(reinterpret_cast<int*>(sc + 2), __float_as_int(fmaxf(rp, rd)));
+      }
+      finish_qp();
+    }
+    __syncthreads();
+    // ---- A6: energy;  A7 (part 1): dE/dG = -2 w_Q sum_j r_j y_j^T
+    // (DFC: E_Q = |G u|^2 with u = 1 on every normal component, so
+    // dE/dG = 2 w_Q (G u) u^T: only the normal columns)
+    if (active && A.dfc) {
+      float gu[6];
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < M; ++i) s += Gs[r * NV + 3 * i];
+        gu[r] = s;
+      }
+      for (int e = lane; e < 6 * NV; e += S) {
+        const int r = e / NV, a = e % NV;
+        float g = 0.f;
+#pragma unroll
+        for (int rr = 0; rr < 6; ++rr) g = (rr == r) ? gu[rr] : g;
+        per[L::oDG + e] = (a % 3 == 0) ? 2.f * A.w_q * g : 0.f;
+      }
+      if (lane == 0) {
+        float EQ = 0.f;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) EQ = fmaf(gu[r], gu[r], EQ);
+        float Ed = 0.f;
+        for (int i = 0; i < M; ++i) {
+          const float r = per[L::oCT + L::CTW * i + 9] - H.alpha - A.delta;
+          Ed = fmaf(r, r, Ed);
+        }
+        float Ec = 0.f;
+        if (A.coll)
+          for (int l = 0; l < S; ++l) Ec += per[L::oGC + MAXD + l];
+        sc[0] = A.w_q * EQ + A.w_d * Ed + Ec;
+      }
+    }
+    if (active && !A.dfc) {
+      const float* ry = per + L::oRY;
+      for (int e = lane; e < 6 * NV; e += S) {
+        const int r = e / NV, a = e % NV;
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;  // independent partial sums
+        int j = 0;
+        for (; j + 3 < S; j += 4) {
+          s0 = fmaf(ry[j * (6 + NV) + r], ry[j * (6 + NV) + 6 + a], s0);
+          s1 = fmaf(ry[(j + 1) * (6 + NV) + r], ry[(j + 1) * (6 + NV) + 6 + a], s1);
+          s2 = fmaf(ry[(j + 2) * (6 + NV) + r], ry[(j + 2) * (6 + NV) + 6 + a], s2);
+          s3 = fmaf(ry[(j + 3) * (6 + NV) + r], ry[(j + 3) * (6 + NV) + 6 + a], s3);
+        }
+        for (; j < S; ++j) s0 = fmaf(ry[j * (6 + NV) + r], ry[j * (6 + NV) + 6 + a], s0);
+        per[L::oDG + e] = -2.f * A.w_q * ((s0 + s1) + (s2 + s3));
+      }
+      if (lane == 0) {
+        float EQ = 0.f;
+        for (int j = 0; j < S; ++j) EQ += per[L::oQ + j];
+        float Ed = 0.f;
+        for (int i = 0; i < M; ++i) {
+          const float r = per[L::oCT + L::CTW * i + 9] - H.alpha - A.delta;
+          Ed = fmaf(r, r, Ed);
+        }
+        float Ec = 0.f;
+        if (A.coll)
+          for (int l = 0; l < S; ++l) Ec += per[L::oGC + MAXD + l];
+        sc[0] = A.w_q * EQ + A.w_d * Ed + Ec;
+      }
+    }
+    __syncthreads();
+    // ---- A7 (part 2): through the contact geometry and the kinematic chain
+    if (active && lane < M) {
+      const ContactGeo k = load_ct(per + L::oCT + L::CTW * lane);
+      float cols[18];
+      for (int r = 0; r < 6; ++r)
+        for (int cc = 0; cc < 3; ++cc) cols[r * 3 + cc] = per[L::oDG + r * NV + 3 * lane + cc];
+      float dEdc[3];
+      contact_adjoint(k, cols, 2.f * A.w_d * (k.phi - H.alpha - A.delta), dEdc);
+      const float* jw = per + L::oJW + lane * MAXCHAIN * 6;  // frames from the forward pass
+      const float* c = k.c;
+      float* cb = per + L::oCB + lane * (6 + MAXCHAIN);
+      cb[0] = dEdc[0];
+      cb[1] = dEdc[1];
+      cb[2] = dEdc[2];
+      // root rotations rx, ry, rz: axes through t
+      {
+        float s1, c1, s2, c2;
+        sincosf(xs[3], &s1, &c1);
+        sincosf(xs[4], &s2, &c2);
+        const float om[3][3] = {{1.f, 0.f, 0.f}, {0.f, c1, s1}, {s2, -s1 * c2, c1 * c2}};
+        const float rel[3] = {c[0] - xs[0], c[1] - xs[1], c[2] - xs[2]};
+        for (int k3 = 0; k3 < 3; ++k3) {
+          float v[3];
+          cross3(om[k3], rel, v);
+          cb[3 + k3] = dEdc[0] * v[0] + dEdc[1] * v[1] + dEdc[2] * v[2];
+        }
+      }
+      const int Lc = H.chain_len[lane];
+      for (int kk = 0; kk < Lc; ++kk) {
+        const float rel[3] = {c[0] - jw[6 * kk + 3], c[1] - jw[6 * kk + 4], c[2] - jw[6 * kk + 5]};
+        float v[3];
+        cross3(jw + 6 * kk, rel, v);
+        cb[6 + kk] = dEdc[0] * v[0] + dEdc[1] * v[1] + dEdc[2] * v[2];
+      }
+    }
+    __syncthreads();
+    // ---- gradient assembly (fixed order over contacts) and A8: Adam + clamp
+    if (active) {
+      const float* cb = per + L::oCB;
+      const int tstep = A.t0 + step + 1;
+      const float c1 = 1.f - powf(A.b1, (float)tstep), c2 = 1.f - powf(A.b2, (float)tstep);
+      for (int k = lane; k < D; k += S) {
+        float g = 0.f;
+        if (k < 6) {
+          for (int i = 0; i < M; ++i) g += cb[i * (6 + MAXCHAIN) + k];
+        } else {
+          for (int i = 0; i < M; ++i) {
+            const int pos = H.jpos[i][k - 6];
+            if (pos >= 0) g += cb[i * (6 + MAXCHAIN) + 6 + pos];
+          }
+        }
+        if (A.coll) g += per[L::oGC + k];
+        if (MODE != MODE_STEP) {
+          if (A.dEdx) A.dEdx[(size_t)b * D + k] = g;
+        } else {
+          const float mm = fmaf(A.b1, ams[k], (1.f - A.b1) * g);
+          const float vv = fmaf(A.b2, avs[k], (1.f - A.b2) * g * g);
+          ams[k] = mm;
+          avs[k] = vv;
+          const float lr = k < 3 ? A.lr_t : A.lr_r;
+          const float xn = xs[k] - lr * (mm / c1) / (sqrtf(vv / c2) + A.adam_eps);
+          xs[k] = fminf(fmaxf(xn, H.qmin[k]), H.qmax[k]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+
+  // ---- write back
+  if (!active) return;
+  if (lane == 0) {
+    if (A.E) A.E[b] = sc[0];
+    if (A.status) A.status[b] = *stat;
+    if (A.res) A.res[b] = sc[2];
+  }
+  if (MODE == MODE_STEP) {
+    for (int k = lane; k < D; k += S) {
+      A.x_state[(size_t)b * D + k] = xs[k];
+      A.am[(size_t)b * D + k] = ams[k];
+      A.av[(size_t)b * D + k] = avs[k];
+    }
+  }
+  if (MODE == MODE_EVAL && A.qy) {
+#pragma unroll
+    for (int a = 0; a < NV; ++a) A.qy[a * NQ + q] = y[a];
+#pragma unroll
+    for (int r = 0; r < NC; ++r) A.qw[r * NQ + q] = w[r];
+  }
+  if (MODE == MODE_EVAL) {
+    if (A.Qout) A.Qout[q] = per[L::oQ + lane];
+    if (A.yout)
+#pragma unroll
+      for (int a = 0; a < NV; ++a) A.yout[q * NV + a] = y[a];
+  }
+}
+
+template <int M, int MODE, int CONE, bool ADAPT>
+__global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  fused_cta<M, MODE, CONE, ADAPT>(A, blockIdx.x, A.gpb, smem);
+}
+
+// ============================================================================ kernel: several jobs in one launch
+// Jobs with different hand templates (m = 3, 4, 5), objects, batch sizes,
+// wrench sets and step counts share one launch: CTA c belongs to the job j
+// with cta_begin[j] <= c < cta_begin[j+1] and runs that job's fused step on
+// its tile of grasps.  The table travels in the kernel parameters, so a
+// launch needs no device memory of its own.
+struct MultiArgs {
+  int n_jobs;
+  int m[BODEX_MAX_JOBS];
+  int cta_begin[BODEX_MAX_JOBS + 1];
+  FusedArgs job[BODEX_MAX_JOBS];
+};
+
+static_assert(sizeof(MultiArgs) <= 32000, "job table must fit in the kernel parameter space");
+
+template <bool ADAPT>
+__global__ void __launch_bounds__(CTA_LANES, 4) multi_kernel(const __grid_constant__ MultiArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  const int c = blockIdx.x;
+  int j = 0;
+  while (j + 1 < A.n_jobs && c >= A.cta_begin[j + 1]) ++j;
+  const FusedArgs& J = A.job[j];
+  const int cta = c - A.cta_begin[j];
+  switch (A.m[j]) {
+    case 3: fused_cta<3, MODE_STEP, CONE_ANY, ADAPT>(J, cta, J.gpb, smem); break;
+    case 4: fused_cta<4, MODE_STEP, CONE_ANY, ADAPT>(J, cta, J.gpb, smem); break;
+    default: fused_cta<5, MODE_STEP, CONE_ANY, ADAPT>(J, cta, J.gpb, smem); break;
+  }
+}
+
+// ============================================================================ launch helpers
+namespace bodex {
+
+// Grasps per CTA: 96 lanes / s, capped by the shared memory one CTA may use.
+template <int M>
+inline int gpb_for(int s) {
+  constexpr size_t kMaxSmem = 227 * 1024;
+  const size_t per = 4u * (size_t)(Lay<M>::KS + Lay<M>::PER);
+  const size_t fit = (kMaxSmem - 4u * Lay<M>::HAND_WORDS) / per;
+  return std::max(1, std::min(CTA_LANES / s, (int)fit));
+}
+
+// Grasps per CTA: the requested count (autotuner), else the default,
+// never more than fit in 96 lanes and in shared memory.
+template <int M>
+inline int pick_gpb(int s, int requested) {
+  const int cap = gpb_for<M>(s);
+  return requested > 0 ? std::min(requested, cap) : cap;
+}
+
+// Raises the kernel's dynamic shared-memory limit when needed, once per
+// device and size (so that launches recorded into a CUDA graph issue no
+// attribute calls after the first).
+template <class K>
+inline int ensure_smem(K kernel, size_t bytes) {
+  // A launch reports errors through cudaGetLastError; clear what an earlier,
+  // already reported failure may have left behind (sticky device faults are
+  // returned again by the next call regardless).
+  (void)cudaGetLastError();
+  if (bytes <= 48 * 1024) return BODEX_OK;
+  static std::mutex mu;
+  static std::map<std::pair<const void*, int>, size_t> configured;  // (kernel, device) -> bytes
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  const auto key = std::make_pair(reinterpret_cast<const void*>(kernel), dev);
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = configured.find(key);
+  if (it != configured.end() && it->second >= bytes) return BODEX_OK;
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) {
+    (void)cudaGetLastError();
+    return cuda_fail(e, "cudaFuncSetAttribute");
+  }
+  configured[key] = bytes;
+  return BODEX_OK;
+}
+
+}  // namespace bodex
+
+template <int M>
+inline int run_fused(int mode, const FusedArgs& A0, cudaStream_t st) {
+  FusedArgs A = A0;
+  A.gpb = pick_gpb<M>(A.S, A0.gpb);
+  const int gpb = A.gpb;
+  const size_t bytes = Lay<M>::bytes(gpb);
+  const dim3 grid((A.B + gpb - 1) / gpb), block(gpb * A.S);
+  if (A.B == 0) return BODEX_OK;
+  const bool soc = A.cfg.cone != 0;
+  const bool adapt = A.cfg.eps > 0.f && A.cfg.adapt;
+  auto go = [&](auto kernel) -> int {
+    if (int r = ensure_smem(kernel, bytes)) return r;
+    kernel<<<grid, block, bytes, st>>>(A);
+    return BODEX_OK;
+  };
+  int r;
+  if (mode == MODE_ADJOINT) r = go(fused_kernel<M, MODE_ADJOINT, CONE_PYR, false>);  // no lower-level solve
+  else if (mode == MODE_STEP)
+    r = soc ? (adapt ? go(fused_kernel<M, MODE_STEP, CONE_SOC, true>) : go(fused_kernel<M, MODE_STEP, CONE_SOC, false>))
+            : (adapt ? go(fused_kernel<M, MODE_STEP, CONE_PYR, true>) : go(fused_kernel<M, MODE_STEP, CONE_PYR, false>));
+  else
+    r = soc ? (adapt ? go(fused_kernel<M, MODE_EVAL, CONE_SOC, true>) : go(fused_kernel<M, MODE_EVAL, CONE_SOC, false>))
+            : (adapt ? go(fused_kernel<M, MODE_EVAL, CONE_PYR, true>) : go(fused_kernel<M, MODE_EVAL, CONE_PYR, false>));
+  if (r) return r;
+  return launch_err("fused_kernel launch");
+}
+
+template <int M>
+inline int run_qp(const float* G, int B, const float* T, int s, const AdmmCfg& cfg, int warm, float* y, float* z,
+           float* lam, float* Q, int32_t* iters, int32_t* status, float* res, cudaStream_t st) {
+  if (B == 0) return BODEX_OK;
+  const int gpb = gpb_for<M>(s);
+  const size_t bytes = Lay<M>::bytes(gpb);
+  if (cfg.cone) {
+    if (int r = ensure_smem(qp_solve_kernel<M, CONE_SOC>, bytes)) return r;
+    qp_solve_kernel<M, CONE_SOC><<<(B + gpb - 1) / gpb, gpb * s, bytes, st>>>(G, B, T, s, cfg, warm, y, z, lam, Q,
+                                                                              iters, status, res);
+  } else {
+    if (int r = ensure_smem(qp_solve_kernel<M, CONE_PYR>, bytes)) return r;
+    qp_solve_kernel<M, CONE_PYR><<<(B + gpb - 1) / gpb, gpb * s, bytes, st>>>(G, B, T, s, cfg, warm, y, z, lam, Q,
+                                                                              iters, status, res);
+  }
+  return launch_err("qp_solve_kernel launch");
+}
+
+// Launchers, one translation unit each (fused_m*.cu, qp.cu, fused_multi.cu).
+int launch_fused_m3(int mode, const FusedArgs& A, cudaStream_t st);
+int launch_fused_m4(int mode, const FusedArgs& A, cudaStream_t st);
+int launch_fused_m5(int mode, const FusedArgs& A, cudaStream_t st);
+int launch_qp(int m, const float* G, int B, const float* T, int s, const AdmmCfg& cfg, int warm, float* y, float* z,
+              float* lam, float* Q, int32_t* iters, int32_t* status, float* res, cudaStream_t st);
+int launch_multi(bool adapt, const MultiArgs& MA, int total, size_t bytes, cudaStream_t st);

@@ -26,6 +26,9 @@ import numpy as np
 from . import Hand, Object, State, bodex_step, bodex_step_multi, step_params
 from ._binding import BODEX_MAX_JOBS
 
+CTA_LANES = 96    # threads per thread block of the fused step kernel
+CTAS_PER_SM = 4   # its resident blocks per SM (register bound)
+
 
 @dataclass
 class JobSpec:
@@ -199,13 +202,19 @@ class Server(_Base):
     fit, pooled states are freed first."""
 
     def __init__(self, params: dict | None = None, qp=None, steps_per_tick: int = 10, hbm_budget: int | None = None,
-                 max_jobs: int = BODEX_MAX_JOBS, grasps_per_cta: int = 0, max_inflight: int = 2):
+                 max_jobs: int = BODEX_MAX_JOBS, grasps_per_cta: int = 0, max_inflight: int = 2,
+                 max_waves: float | None = 1.0):
         super().__init__(params, qp, grasps_per_cta)
         import torch
         if hbm_budget is None:
             free, _ = torch.cuda.mem_get_info()
             hbm_budget = int(free * 0.8)
         self.hbm_budget = int(hbm_budget)
+        # thread blocks resident at once: a launch beyond one wave slows every
+        # job in it, so admission stops there (None: no limit)
+        sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+        self.cta_budget = None if max_waves is None else max(1, int(max_waves * sms * CTAS_PER_SM))
+        self.ctas = 0
         self.steps_per_tick = int(steps_per_tick)
         self.max_jobs = min(int(max_jobs), BODEX_MAX_JOBS)
         self.max_inflight = max(1, int(max_inflight))
@@ -221,6 +230,10 @@ class Server(_Base):
 
     def busy(self) -> bool:
         return bool(self.active or self._waiting or self.finishing)
+
+    def _job_ctas(self, spec) -> int:
+        gpb = self.params.grasps_per_cta or max(1, CTA_LANES // spec.T.shape[0])
+        return -(-spec.x0.shape[0] // gpb)
 
     def _new_state(self, spec, hand) -> State:
         lst = self.pool.get(_state_key(spec))
@@ -252,11 +265,15 @@ class Server(_Base):
                 if not self.active and not self.finishing and nb > self.hbm_budget:
                     raise MemoryError(f"job {jid} needs {nb} bytes, over the HBM budget {self.hbm_budget}")
                 break  # wait for memory to free up
+            nc = self._job_ctas(spec)
+            if self.cta_budget is not None and self.active and self.ctas + nc > self.cta_budget:
+                break  # wait for a wave's worth of thread blocks to free up
             with self._lock:
                 self._waiting.popleft()
             self.active.append(self._open(jid, spec))
             self.active[-1].nbytes = job_bytes(spec)
             self.used += nb
+            self.ctas += nc
             self.peak_active = max(self.peak_active, len(self.active) + len(self.finishing))
             self.peak_used = max(self.peak_used, self.used + self.pooled)
 
@@ -300,6 +317,7 @@ class Server(_Base):
         keep = []
         for a in self.active:
             if a.remaining == 0:
+                self.ctas -= self._job_ctas(a.spec)
                 xh = torch.empty((a.spec.x0.shape[0], a.hand.D), dtype=torch.float32).pin_memory()
                 Eh = torch.empty(a.spec.x0.shape[0], dtype=torch.float32).pin_memory()
                 xh.copy_(a.state.pose(), non_blocking=True)

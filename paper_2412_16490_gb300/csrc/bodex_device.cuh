@@ -437,9 +437,10 @@ __device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(
 __device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
 
 // Entry e (0..27, row-major upper triangle of the 7x7) of M = I + V^T Dg^-1 V,
-// accumulated in precision R.
+// accumulated in precision R; idn / idt are 1 / Dg of a normal / a
+// tangential component.
 template <int M, typename R>
-__device__ inline R woodbury_M_entry(const float* G, int e, const AdmmCfg& c, const DiagK& dk) {
+__device__ inline R woodbury_M_entry(const float* G, int e, const AdmmCfg& c, R idn, R idt) {
   constexpr int NV = 3 * M;
   int a = 0, b = 0, k = e;
   for (a = 0; a < 7; ++a) {
@@ -449,41 +450,66 @@ __device__ inline R woodbury_M_entry(const float* G, int e, const AdmmCfg& c, co
     }
     k -= 7 - a;
   }
-  const R idn = R(1) / R(dk.dn), idt = R(1) / R(dk.dt);
-  R s = 0;
-  if (b < 6) {  // both columns from sqrt2 G^T
-    for (int i = 0; i < NV; ++i) s = fma_r(R(G[a * NV + i]) * R(G[b * NV + i]), (i % 3 == 0) ? idn : idt, s);
-    return fma_r(R(2), s, a == b ? R(1) : R(0));
+  if (b < 6) {  // both columns from sqrt2 G^T: normal and tangential parts summed apart
+    R sn = 0, st = 0;
+#pragma unroll
+    for (int i = 0; i < NV; i += 3) {
+      sn = fma_r(R(G[a * NV + i]), R(G[b * NV + i]), sn);
+      st = fma_r(R(G[a * NV + i + 1]), R(G[b * NV + i + 1]), st);
+      st = fma_r(R(G[a * NV + i + 2]), R(G[b * NV + i + 2]), st);
+    }
+    return fma_r(R(2), fma_r(sn, idn, st * idt), a == b ? R(1) : R(0));
   }
+  R s = 0;
   if (a < 6) {  // sqrt2 G^T against sqrt(rho) u
+#pragma unroll
     for (int i = 0; i < NV; i += 3) s += R(G[a * NV + i]);
     return s * (sqrt(R(2) * R(c.rho)) * idn);
   }
   return fma_r(R(c.rho) * R(M), idn, R(1));
 }
 
-// Scratch (in floats) that setup_kinv_woodbury<M, R> needs.
+// Scratch (in floats) that setup_kinv_woodbury<M, R> needs: M (28), then U
+// in rows of 8 (16-byte aligned when the scratch is).
 template <int M, typename R>
 struct WoodburyScratch {
   static constexpr int floats = (28 + 8 * 3 * M) * (int)(sizeof(R) / 4);
 };
+
+// Row i of U (7 entries, stored in a row of 8) in registers.
+template <typename R>
+__device__ __forceinline__ void load_u_row(const R* Us, int i, R (&u)[7]) {
+  if constexpr (sizeof(R) == 4) {
+    const float4 lo = *reinterpret_cast<const float4*>(Us + 8 * i);
+    const float4 hi = *reinterpret_cast<const float4*>(Us + 8 * i + 4);
+    u[0] = lo.x, u[1] = lo.y, u[2] = lo.z, u[3] = lo.w, u[4] = hi.x, u[5] = hi.y, u[6] = hi.z;
+  } else {
+#pragma unroll
+    for (int a = 0; a < 7; a += 2) {
+      const double2 v = *reinterpret_cast<const double2*>(Us + 8 * i + a);
+      u[a] = v.x;
+      if (a + 1 < 7) u[a + 1] = v.y;
+    }
+  }
+}
 
 // Writes alpha K^-1 (alpha: the ADMM relaxation; packed upper triangle, see
 // Admm<M>::tri; rounded to float) for one grasp,
 // computed in precision R: float for the fixed-iteration step loop, double
 // when the solve iterates to a residual target (the ADMM fixed point moves
 // with the backward error of the inverse: the dual residual floor is
-// |(K^-1_computed)^-1 - K| |y|).  Must be called by every thread of the CTA
-// (contains barriers).
+// |(K^-1_computed)^-1 - K| |y|).  The scratch must be 16-byte aligned.
+// Must be called by every thread of the CTA (contains barriers).
 template <int M, typename R>
 __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const float* G, float* scratch, float* Kinv,
                                            const AdmmCfg& c) {
-  constexpr int NV = 3 * M;
+  constexpr int NV = 3 * M, NTRI = Admm<M>::NTRI;
   const DiagK dk = diag_k(c);
   R* Ms = reinterpret_cast<R*>(scratch);  // 28
   R* Us = Ms + 28;                        // NV rows of 8
+  const R idn = R(1) / R(dk.dn), idt = R(1) / R(dk.dt);
   if (active)
-    for (int e = lane; e < 28; e += S) Ms[e] = woodbury_M_entry<M, R>(G, e, c, dk);
+    for (int e = lane; e < 28; e += S) Ms[e] = woodbury_M_entry<M, R>(G, e, c, idn, idt);
   __syncthreads();
   if (active) {
     // 7x7 Cholesky, replicated in every lane (registers).  Index (a, b),
@@ -493,6 +519,7 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
 #pragma unroll
     for (int e = 0; e < 28; ++e) L[e] = Ms[e];
     auto idx = [](int a, int b) { return a * 7 - (a * (a - 1)) / 2 + (b - a); };
+    R ild[7];  // reciprocals of the diagonal of L
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
       R d = L[idx(j, j)];
@@ -501,6 +528,7 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
       const R ljj = sqrt(d > R(1e-30) ? d : R(1e-30));
       L[idx(j, j)] = ljj;
       const R il = R(1) / ljj;
+      ild[j] = il;
 #pragma unroll
       for (int i = j + 1; i < 7; ++i) {
         R t = L[idx(j, i)];
@@ -510,11 +538,8 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
       }
     }
     const R s2 = sqrt(R(2)), sr = sqrt(R(c.rho));
-    R ild[7];  // reciprocals of the diagonal of L
-#pragma unroll
-    for (int a = 0; a < 7; ++a) ild[a] = R(1) / L[idx(a, a)];
     for (int i = lane; i < NV; i += S) {
-      const R id = R(1) / R((i % 3 == 0) ? dk.dn : dk.dt);
+      const R id = (i % 3 == 0) ? idn : idt;
       R w[7];
 #pragma unroll
       for (int a = 0; a < 6; ++a) w[a] = s2 * R(G[a * NV + i]) * id;
@@ -532,19 +557,24 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
     }
   }
   __syncthreads();
-  if (active)
-    for (int i = lane; i < NV; i += S) {
-      R ui[7];
+  // alpha K^-1 = alpha (Dg^-1 - U U^T): the NTRI packed entries spread evenly
+  // over the grasp's lanes (entry t = (i, j) of the row-major upper triangle)
+  if (active) {
+    int i = 0, j = lane;  // entry `lane`, then every S-th
+    while (i < NV && j >= NV) j -= NV - 1 - i++;
+    for (int t = lane; t < NTRI; t += S) {
+      R ui[7], uj[7];
+      load_u_row(Us, i, ui);
+      load_u_row(Us, j, uj);
+      R acc = 0;
 #pragma unroll
-      for (int a = 0; a < 7; ++a) ui[a] = Us[i * 8 + a];
-      const R id = R(1) / R((i % 3 == 0) ? dk.dn : dk.dt);
-      for (int j = i; j < NV; ++j) {
-        R t = 0;
-#pragma unroll
-        for (int a = 0; a < 7; ++a) t = fma_r(ui[a], Us[j * 8 + a], t);
-        Kinv[Admm<M>::tri(i, j)] = (float)(R(c.alpha) * ((i == j ? id : R(0)) - t));
-      }
+      for (int a = 0; a < 7; ++a) acc = fma_r(ui[a], uj[a], acc);
+      const R dg = i == j ? ((i % 3 == 0) ? idn : idt) : R(0);
+      Kinv[t] = (float)(R(c.alpha) * (dg - acc));
+      j += S;  // advance to entry t + S
+      while (i < NV && j >= NV) j -= NV - 1 - i++;
     }
+  }
   __syncthreads();
 }
 

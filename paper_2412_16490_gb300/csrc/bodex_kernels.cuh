@@ -41,7 +41,7 @@ struct Lay {
   static constexpr int KS = KT + ((20 - KT % 32) + 32) % 32;
   static constexpr int CTW = 24;  // floats per contact record
   static constexpr int oG = 0;
-  static constexpr int oK = oG + 6 * NV;  // K^-1 setup scratch
+  static constexpr int oK = align4(oG + 6 * NV);  // K^-1 setup scratch (16-byte aligned)
   static constexpr int oCT = oK + WoodburyScratch<M, double>::floats;
   static constexpr int oRY = oCT + CTW * M;
   static constexpr int oQ = oRY + SMAX * (6 + NV);

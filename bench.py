@@ -272,6 +272,7 @@ def run_ours(args, rank, world, local_rank):
         extra["qp_solves"]["adaptive_rho"] = True
         extra["qp_solves"]["fixed_rho"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev)
         extra["qp_solves_elliptic_cone"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev, cone=bx.CONE_ELLIPTIC)
+        extra["qp_solves_warm_in_loop"] = qp_solve_rate_warm(bx, torch, H, Ob, x_dev, T_dev, P)
         extra["e2e"] = e2e_rate(bx, torch, H, Ob, st, x0, T_dev, sp)
         extra["persistent_mixed"] = persistent_mixed(bx, torch, P)
         if args.serve_jobs > 0:
@@ -561,6 +562,44 @@ def qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev, cone=0, adaptive_rho=0):
     return {"value": float(conv.sum().item()) / dt, "unit": "QP solves/s (converged to 1e-5)",
             "qps": int(conv.numel()), "converged_frac": float(conv.float().mean().item()),
             "iters_median": float(it.median().item()), "iters_max": int(it.max().item()), "ms": dt * 1e3}
+
+
+def qp_solve_rate_warm(bx, torch, H, Ob, x_dev, T_dev, P, adaptive_rho=1, at_step=100):
+    """The in-loop rate: the same 49152 QPs halfway through a 200-step run,
+    warm-started from the previous upper step's solution (as the step loop
+    does), to 1e-5 (cap 5000).  Poses x_t and x_(t+1) come from the fused
+    step loop (50 ADMM iterations per step); the QPs at x_t are solved cold
+    first to give the warm start."""
+    B, s = x_dev.shape[0], T_dev.shape[0]
+    st = bx.State(H, B, s)
+    st.set_pose(x_dev)
+    sp = bx.step_params(P, qp=bx.qp_params(max_iter=50))
+    bx.bodex_step(H, Ob, st, T_dev, at_step, sp)
+    x_t = st.pose().clone()
+    bx.bodex_step(H, Ob, st, T_dev, 1, sp)
+    x_t1 = st.pose().clone()
+    cold = bx.qp_params(eps_abs=1e-5, max_iter=5000, check_every=10, adaptive_rho=adaptive_rho)
+    prev = bx.bodex_qp_solve_batch(bx.bodex_fk_contacts(H, Ob, x_t)["G"], T_dev, cold)
+    G1 = bx.bodex_fk_contacts(H, Ob, x_t1)["G"]
+    warm = bx.qp_params(eps_abs=1e-5, max_iter=5000, check_every=10, adaptive_rho=adaptive_rho, warm=1)
+    start = lambda: [prev[k].clone() for k in ("y", "z", "lam")]
+    bx.bodex_qp_solve_batch(G1, T_dev, warm, *start())  # warm-up
+    y, z, lam = start()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    out = bx.bodex_qp_solve_batch(G1, T_dev, warm, y, z, lam)
+    b.record()
+    torch.cuda.synchronize()
+    dt = a.elapsed_time(b) / 1e3
+    conv = ((out["status"] & bx.ST_NOT_CONVERGED) == 0)
+    it = out["iters"].float()
+    cold_it = bx.bodex_qp_solve_batch(G1, T_dev, cold)["iters"].float()
+    return {"value": float(conv.sum().item()) / dt, "unit": "QP solves/s (converged to 1e-5, warm start)",
+            "qps": int(conv.numel()), "at_upper_step": at_step, "converged_frac": float(conv.float().mean().item()),
+            "iters_median": float(it.median().item()), "iters_max": int(it.max().item()),
+            "cold_iters_median_same_qps": float(cold_it.median().item()), "ms": dt * 1e3,
+            "adaptive_rho": bool(adaptive_rho)}
 
 
 def e2e_rate(bx, torch, H, Ob, st, x0, T_dev, sp, reps=3):

@@ -511,15 +511,17 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
   if (active)
     for (int e = lane; e < 28; e += S) Ms[e] = woodbury_M_entry<M, R>(G, e, c, idn, idt);
   __syncthreads();
-  if (active) {
-    // 7x7 Cholesky, replicated in every lane (registers).  Index (a, b),
-    // a <= b, of the row-major upper triangle; after factoring, entry (a, b)
-    // holds L[b][a].
-    R L[28];
+  // 7x7 Cholesky.  Index (a, b), a <= b, of the row-major upper triangle;
+  // after factoring, entry (a, b) holds L[b][a].  In float every lane
+  // factors its own copy in registers (no barrier); in double, whose
+  // arithmetic is far slower, lane 0 factors it once into the shared M and
+  // ild (in Us' padding column) and the lanes read it back.
+  auto idx = [](int a, int b) { return a * 7 - (a * (a - 1)) / 2 + (b - a); };
+  R L[28];
+  R ild[7];  // reciprocals of the diagonal of L
+  auto factor = [&]() {
 #pragma unroll
     for (int e = 0; e < 28; ++e) L[e] = Ms[e];
-    auto idx = [](int a, int b) { return a * 7 - (a * (a - 1)) / 2 + (b - a); };
-    R ild[7];  // reciprocals of the diagonal of L
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
       R d = L[idx(j, j)];
@@ -537,6 +539,26 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
         L[idx(j, i)] = t * il;
       }
     }
+  };
+  if constexpr (sizeof(R) == 8) {
+    if (active && lane == 0) {
+      factor();
+#pragma unroll
+      for (int e = 0; e < 28; ++e) Ms[e] = L[e];
+#pragma unroll
+      for (int a = 0; a < 7; ++a) Us[a * 8 + 7] = ild[a];
+    }
+    __syncthreads();
+    if (active) {
+#pragma unroll
+      for (int e = 0; e < 28; ++e) L[e] = Ms[e];
+#pragma unroll
+      for (int a = 0; a < 7; ++a) ild[a] = Us[a * 8 + 7];  // the U rows below write entries 0..6 only
+    }
+  } else {
+    if (active) factor();
+  }
+  if (active) {
     const R s2 = sqrt(R(2)), sr = sqrt(R(c.rho));
     for (int i = lane; i < NV; i += S) {
       const R id = (i % 3 == 0) ? idn : idt;
@@ -624,7 +646,7 @@ __device__ __forceinline__ void At_contact(float v0, const float (&vk)[8], float
 
 template <int M>
 __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* mq, const float* Kinv,
-                                               const AdmmCfg& c) {
+                                               const AdmmCfg& c, float rho) {
   constexpr int NV = Admm<M>::NV;
   // rhs = sigma y - q + rho A^T v,  v = 2 Pi(w) - w, one contact at a time
   float rhs[NV];
@@ -639,9 +661,9 @@ __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* 
     for (int k = 0; k < 8; ++k) vk[k] = -fabsf(w[9 * i + 1 + k]);
     float gn, gd, ge;
     At_contact(v0, vk, c.mu_c8, gn, gd, ge);
-    rhs[3 * i] = fmaf(c.sigma, y[3 * i], fmaf(c.rho, gn, mq[3 * i]));
-    rhs[3 * i + 1] = fmaf(c.sigma, y[3 * i + 1], fmaf(c.rho, gd, mq[3 * i + 1]));
-    rhs[3 * i + 2] = fmaf(c.sigma, y[3 * i + 2], fmaf(c.rho, ge, mq[3 * i + 2]));
+    rhs[3 * i] = fmaf(c.sigma, y[3 * i], fmaf(rho, gn, mq[3 * i]));
+    rhs[3 * i + 1] = fmaf(c.sigma, y[3 * i + 1], fmaf(rho, gd, mq[3 * i + 1]));
+    rhs[3 * i + 2] = fmaf(c.sigma, y[3 * i + 2], fmaf(rho, ge, mq[3 * i + 2]));
   }
   // yt = alpha K^-1 rhs from the packed upper triangle, column by column:
   // entry (a, b), a <= b, adds K_ab rhs_b to yt_a and, off the diagonal,
@@ -687,7 +709,7 @@ __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* 
 // z = Pi(w), lam = rho (w - Pi(w)).
 template <int M>
 __device__ inline void admm_residuals(const float* y, const float* w, const float* mq, const float* G,
-                                      const AdmmCfg& c, float& rp, float& rd) {
+                                      const AdmmCfg& c, float rho, float& rp, float& rd) {
   constexpr int NV = Admm<M>::NV;
   rp = 0.f;
   float sumn = 0.f;
@@ -711,14 +733,14 @@ __device__ inline void admm_residuals(const float* y, const float* w, const floa
     for (int a = 0; a < NV; ++a) s = fmaf(lds32(G + r * NV + a), y[a], s);
     gy[r] = s;
   }
-  const float lsum = c.rho * (w[9 * M] - fmaxf(w[9 * M], c.gamma));
+  const float lsum = rho * (w[9 * M] - fmaxf(w[9 * M], c.gamma));
   rd = 0.f;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
-    const float l0 = fmaf(c.rho, w[9 * i] - fminf(fmaxf(w[9 * i], 0.f), 1.f), lsum);
+    const float l0 = fmaf(rho, w[9 * i] - fminf(fmaxf(w[9 * i], 0.f), 1.f), lsum);
     float lk[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) lk[k] = c.rho * (w[9 * i + 1 + k] - fminf(w[9 * i + 1 + k], 0.f));
+    for (int k = 0; k < 8; ++k) lk[k] = rho * (w[9 * i + 1 + k] - fminf(w[9 * i + 1 + k], 0.f));
     float at[3];
     At_contact(l0, lk, c.mu_c8, at[0], at[1], at[2]);
 #pragma unroll
@@ -774,7 +796,7 @@ __device__ __forceinline__ void proj_soc(float s, float u1, float u2, float& ps,
 
 template <int M>
 __device__ __forceinline__ void admm_iteration_soc(float* y, float* w, const float* mq, const float* Kinv,
-                                                   const AdmmCfg& c) {
+                                                   const AdmmCfg& c, float rho) {
   constexpr int NV = Admm<M>::NV;
   // rhs = sigma y - q + rho A^T (2 Pi(w) - w), keeping Pi of the cone rows
   float rhs[NV], pc[3 * M];
@@ -786,9 +808,9 @@ __device__ __forceinline__ void admm_iteration_soc(float* y, float* w, const flo
     const float v0 = fmaf(2.f, __saturatef(wi[0]), -wi[0]) + vsum;
     const float gn = fmaf(c.mu, fmaf(2.f, pc[3 * i], -wi[1]), v0);
     const float gd = fmaf(2.f, pc[3 * i + 1], -wi[2]), ge = fmaf(2.f, pc[3 * i + 2], -wi[3]);
-    rhs[3 * i] = fmaf(c.sigma, y[3 * i], fmaf(c.rho, gn, mq[3 * i]));
-    rhs[3 * i + 1] = fmaf(c.sigma, y[3 * i + 1], fmaf(c.rho, gd, mq[3 * i + 1]));
-    rhs[3 * i + 2] = fmaf(c.sigma, y[3 * i + 2], fmaf(c.rho, ge, mq[3 * i + 2]));
+    rhs[3 * i] = fmaf(c.sigma, y[3 * i], fmaf(rho, gn, mq[3 * i]));
+    rhs[3 * i + 1] = fmaf(c.sigma, y[3 * i + 1], fmaf(rho, gd, mq[3 * i + 1]));
+    rhs[3 * i + 2] = fmaf(c.sigma, y[3 * i + 2], fmaf(rho, ge, mq[3 * i + 2]));
   }
   // yt = alpha K^-1 rhs (packed upper triangle, column order as in admm_iteration)
   float yt[NV];
@@ -823,7 +845,7 @@ __device__ __forceinline__ void admm_iteration_soc(float* y, float* w, const flo
 
 template <int M>
 __device__ inline void admm_residuals_soc(const float* y, const float* w, const float* mq, const float* G,
-                                          const AdmmCfg& c, float& rp, float& rd) {
+                                          const AdmmCfg& c, float rho, float& rp, float& rd) {
   constexpr int NV = Admm<M>::NV;
   rp = 0.f;
   float sumn = 0.f;
@@ -840,13 +862,13 @@ __device__ inline void admm_residuals_soc(const float* y, const float* w, const 
     rp = fmaxf(rp, fabsf(fmaf(c.mu, yn, -ps)));
     rp = fmaxf(rp, fabsf(yd - p1));
     rp = fmaxf(rp, fabsf(ye - p2));
-    lam[4 * i] = c.rho * (wi[0] - p0);
-    lam[4 * i + 1] = c.rho * (wi[1] - ps);
-    lam[4 * i + 2] = c.rho * (wi[2] - p1);
-    lam[4 * i + 3] = c.rho * (wi[3] - p2);
+    lam[4 * i] = rho * (wi[0] - p0);
+    lam[4 * i + 1] = rho * (wi[1] - ps);
+    lam[4 * i + 2] = rho * (wi[2] - p1);
+    lam[4 * i + 3] = rho * (wi[3] - p2);
   }
   rp = fmaxf(rp, fabsf(sumn - fmaxf(w[4 * M], c.gamma)));
-  const float lsum = c.rho * (w[4 * M] - fmaxf(w[4 * M], c.gamma));
+  const float lsum = rho * (w[4 * M] - fmaxf(w[4 * M], c.gamma));
   float gy[6];
 #pragma unroll
   for (int r = 0; r < 6; ++r) {
@@ -891,12 +913,12 @@ template <int M, int CONE>
 __device__ inline int admm_solve(float* y, float* w, const float* mq, const float* Kinv, const float* G,
                                  const AdmmCfg& c, float& rp, float& rd, bool& conv) {
   auto iterate = [&]() {
-    if (CONE == CONE_SOC) admm_iteration_soc<M>(y, w, mq, Kinv, c);
-    else admm_iteration<M>(y, w, mq, Kinv, c);
+    if (CONE == CONE_SOC) admm_iteration_soc<M>(y, w, mq, Kinv, c, c.rho);
+    else admm_iteration<M>(y, w, mq, Kinv, c, c.rho);
   };
   auto residuals = [&]() {
-    if (CONE == CONE_SOC) admm_residuals_soc<M>(y, w, mq, G, c, rp, rd);
-    else admm_residuals<M>(y, w, mq, G, c, rp, rd);
+    if (CONE == CONE_SOC) admm_residuals_soc<M>(y, w, mq, G, c, c.rho, rp, rd);
+    else admm_residuals<M>(y, w, mq, G, c, c.rho, rp, rd);
   };
   int it = 0;
   conv = false;
@@ -973,12 +995,12 @@ __device__ inline int admm_solve_adaptive(bool active, int lane, int S, float* y
       const int chunk = min(c.check, c.iters - it);
 #pragma unroll 1
       for (int k = 0; k < chunk; ++k) {
-        if (CONE == CONE_SOC) admm_iteration_soc<M>(y, w, mq, Kinv, c);
-        else admm_iteration<M>(y, w, mq, Kinv, c);
+        if (CONE == CONE_SOC) admm_iteration_soc<M>(y, w, mq, Kinv, c, c.rho);
+        else admm_iteration<M>(y, w, mq, Kinv, c, c.rho);
       }
       it += chunk;
-      if (CONE == CONE_SOC) admm_residuals_soc<M>(y, w, mq, G, c, rp, rd);
-      else admm_residuals<M>(y, w, mq, G, c, rp, rd);
+      if (CONE == CONE_SOC) admm_residuals_soc<M>(y, w, mq, G, c, c.rho, rp, rd);
+      else admm_residuals<M>(y, w, mq, G, c, c.rho, rp, rd);
       conv = rp <= c.eps && rd <= c.eps;
     }
     const bool done = conv || it >= c.iters;
@@ -1000,7 +1022,8 @@ __device__ inline int admm_solve_adaptive(bool active, int lane, int S, float* y
       rho_new = fminf(fmaxf(c.rho * __expf(sh / cnt), 1e-6f), 1e6f);
       upd = rho_new != c.rho;
     }
-    __syncthreads();  // votes read before the next round writes them
+    // votes read before the next round writes them; no rebuild when no grasp of the CTA moved
+    if (!__syncthreads_or(upd)) continue;
     if (upd) {
       rescale_w<M, CONE>(w, c.rho / rho_new, c);
       c.rho = rho_new;

@@ -117,94 +117,241 @@ __device__ inline void setup_kinv(bool active, int lane, int S, const float* Gs,
 }
 
 // ============================================================================ kernel: batched QP
+// One QP per thread, the grasps' K^-1 shared by their QPs.  QPs converge
+// after very different iteration counts (at 1e-5 on the paper geometry the
+// median is 400, the slowest of a warp's 32 about 1700), and a warp runs
+// until its last QP stops.  So at every residual check the QPs still running
+// are repacked, through shared memory, into the lowest warps of the CTA: a
+// warp whose QPs all stopped waits at the barrier and issues nothing while
+// the others iterate.  A QP carries its iterate, -q, its iteration count and
+// its slot (grasp, wrench); K^-1, G and rho stay with the grasp.
+//
+// Shared memory: alpha K^-1 per grasp (stride as in the fused kernel), the
+// per-grasp block (G, Woodbury scratch, votes, rho), the parking area (one
+// record per QP) and one count per warp.
 template <int M, int CONE>
-__global__ void __launch_bounds__(CTA_LANES) qp_solve_kernel(const float* __restrict__ Gin, int B,
-                                                             const float* __restrict__ T, int S, AdmmCfg cfg,
-                                                             int warm, float* yio, float* zio, float* lio,
-                                                             float* Qout, int32_t* iters_out, int32_t* status_out,
-                                                             float* res_out) {
-  using L = Lay<M>;
-  constexpr int NV = L::NV, NC = CONE == CONE_SOC ? 4 * M + 1 : L::NC;  // ADMM rows
+struct LayQP {
+  static constexpr int NV = 3 * M, NC = CONE == CONE_SOC ? 4 * M + 1 : 9 * M + 1;
+  static constexpr int KS = Lay<M>::KS;
+  static constexpr int oG = 0;
+  static constexpr int oK = align4(6 * NV);  // Woodbury scratch (16-byte aligned)
+  static constexpr int oVote = oK + WoodburyScratch<M, double>::floats;
+  static constexpr int oRho = oVote + SMAX;  // the grasp's rho; oRho + 1: its rho before the last vote
+  static constexpr int PER0 = align4(oRho + 2);
+  static constexpr int PER = PER0 + ((12 - PER0 % 32) + 32) % 32;
+  // parked QP: y, w, -q, then (iterations, slot); an odd count of float4s
+  // per record keeps eight consecutive records on distinct banks
+  static constexpr int pW = align4(NV), pM = pW + align4(NC), pI = pM + align4(NV);
+  static constexpr int PW0 = pI + 4;
+  static constexpr int PW = (PW0 / 4) % 2 ? PW0 : PW0 + 4;
+  static size_t bytes(int gpb, int s) { return 4u * ((size_t)gpb * (KS + PER) + (size_t)gpb * s * PW + 32); }
+};
+
+template <int M, int CONE>
+__global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __restrict__ Gin, int B,
+                                                                const float* __restrict__ T, int S, AdmmCfg cfg,
+                                                                int warm, float* yio, float* zio, float* lio,
+                                                                float* Qout, int32_t* iters_out, int32_t* status_out,
+                                                                float* res_out) {
+  using L = LayQP<M, CONE>;
+  constexpr int NV = L::NV, NC = L::NC;
   extern __shared__ __align__(16) float smem[];
   const int GPB = blockDim.x / S;
+  // setup role of this thread: lane `lane` of grasp gl of the CTA
   const int gl = threadIdx.x / S, lane = threadIdx.x % S;
-  const int b = blockIdx.x * GPB + gl;
-  const bool active = (gl < GPB) && (b < B);
-  float* kin = smem + L::HAND_WORDS + gl * L::KS;
-  float* per = smem + L::HAND_WORDS + GPB * L::KS + gl * L::PER;
-  float* Gs = per + L::oG;
-  int* stat = reinterpret_cast<int*>(per + L::oSC + 1);
-  if (active) {
-    for (int e = lane; e < 6 * NV; e += S) Gs[e] = Gin[(size_t)b * 6 * NV + e];
-    if (lane == 0) *stat = 0;
+  const bool role = (gl < GPB) && (blockIdx.x * GPB + gl < B);
+  float* const park = smem + GPB * (L::KS + L::PER);
+  int* const wcount = reinterpret_cast<int*>(park + GPB * S * L::PW);
+  auto kin = [&](int g) { return smem + g * L::KS; };
+  auto per = [&](int g) { return smem + GPB * L::KS + g * L::PER; };
+  if (role) {
+    const size_t b = (size_t)blockIdx.x * GPB + gl;
+    for (int e = lane; e < 6 * NV; e += S) per(gl)[L::oG + e] = Gin[b * 6 * NV + e];
+    if (lane == 0) per(gl)[L::oRho] = per(gl)[L::oRho + 1] = cfg.rho;
   }
   __syncthreads();
-  setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg);
-  // solves with a residual target adapt rho per grasp, which needs every
-  // thread at the barriers; otherwise idle threads leave here
+  setup_kinv<M>(role, lane, S, per(gl) + L::oG, per(gl) + L::oK, kin(gl), cfg);
   const bool adaptive = cfg.eps > 0.f && cfg.adapt;  // uniform
-  if (!active && !adaptive) return;
-  const size_t q = (size_t)b * S + lane;
+  const int check = cfg.eps > 0.f ? cfg.check : cfg.iters;  // without a target: residuals once, at the end
+  const size_t q0 = (size_t)blockIdx.x * GPB * S;         // first QP of the CTA
+  // the QP this thread runs: slot p = g * S + j of the CTA (at first its own), -1 for none
+  int p = role ? (int)threadIdx.x : -1;
+  int it = 0;
   float y[NV], w[NC], mq[NV];
-  float t[6];
-  if (active) {
+  if (p >= 0) {
+    float t[6];
+#pragma unroll
     for (int r = 0; r < 6; ++r) t[r] = T[lane * 6 + r];
-    neg_q<M>(Gs, t, cfg.beta, mq);
+    neg_q<M>(per(gl) + L::oG, t, cfg.beta, mq);
+    const size_t q = q0 + p;
+    if (warm) {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) y[a] = yio[q * NV + a];
+#pragma unroll
+      for (int r = 0; r < NC; ++r) w[r] = zio[q * NC + r] + lio[q * NC + r] / cfg.rho;
+    } else {
+#pragma unroll
+      for (int a = 0; a < NV; ++a) y[a] = 0.f;
+#pragma unroll
+      for (int r = 0; r < NC; ++r) w[r] = 0.f;
+    }
   }
-  if (!active) {
-  } else if (warm) {
+  // y, z = Pi(w), lam = rho (w - Pi(w)), Q, iterations, residuals and status of slot pp
+  auto finish = [&](int pp, float rp, float rd, bool conv) {
+    const int g = pp / S, j = pp % S;
+    const size_t q = q0 + pp;
+    const float* Gg = per(g) + L::oG;
+    const float rho = per(g)[L::oRho];
+    float Q = 0.f;
+    bool fin = true;
 #pragma unroll
-    for (int a = 0; a < NV; ++a) y[a] = yio[q * NV + a];
+    for (int r = 0; r < 6; ++r) {
+      float s = cfg.beta * T[j * 6 + r];
 #pragma unroll
-    for (int r = 0; r < NC; ++r) w[r] = zio[q * NC + r] + lio[q * NC + r] / cfg.rho;
-  } else {
+      for (int a = 0; a < NV; ++a) s = fmaf(-Gg[r * NV + a], y[a], s);
+      Q = fmaf(s, s, Q);
+    }
 #pragma unroll
-    for (int a = 0; a < NV; ++a) y[a] = 0.f;
+    for (int a = 0; a < NV; ++a) {
+      yio[q * NV + a] = y[a];
+      fin = fin && isfinite(y[a]);
+      Q = fmaf(cfg.eps_reg * y[a], y[a], Q);  // regularised value when eps_reg > 0
+    }
 #pragma unroll
-    for (int r = 0; r < NC; ++r) w[r] = 0.f;
+    for (int r = 0; r < NC; ++r) {
+      const float pr = CONE == CONE_SOC ? proj_row_soc<M>(w, r, cfg.gamma) : proj_row<M>(w[r], r, cfg.gamma);
+      zio[q * NC + r] = pr;
+      lio[q * NC + r] = rho * (w[r] - pr);
+    }
+    Qout[q] = Q;
+    if (iters_out) iters_out[q] = it;
+    if (res_out) {
+      res_out[2 * q] = rp;
+      res_out[2 * q + 1] = rd;
+    }
+    int st = 0;
+    if (!fin || !isfinite(Q)) st |= BODEX_ST_NONFINITE;
+    if (cfg.eps > 0.f && !conv) st |= BODEX_ST_NOT_CONVERGED;
+    if (status_out) status_out[q] = st;
+  };
+  // parking record r: the iterate, -q, the iteration count and the slot
+  auto park_store = [&](int r) {
+    float* rec = park + r * L::PW;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) rec[a] = y[a];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) rec[L::pW + k] = w[k];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) rec[L::pM + a] = mq[a];
+    reinterpret_cast<int*>(rec)[L::pI] = it;
+    reinterpret_cast<int*>(rec)[L::pI + 1] = p;
+  };
+  auto park_load = [&](int r) {
+    const float* rec = park + r * L::PW;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) y[a] = rec[a];
+#pragma unroll
+    for (int k = 0; k < NC; ++k) w[k] = rec[L::pW + k];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) mq[a] = rec[L::pM + a];
+    it = reinterpret_cast<const int*>(rec)[L::pI];
+    p = reinterpret_cast<const int*>(rec)[L::pI + 1];
+  };
+  const int warp = threadIdx.x / 32, wl = threadIdx.x % 32;
+  const int nw = min(32, (int)blockDim.x - 32 * warp);
+  const unsigned wmask = nw == 32 ? 0xffffffffu : (1u << nw) - 1u;  // this warp's threads
+  int warps = (blockDim.x + 31) / 32;                                  // warps that hold running QPs
+#pragma unroll 1
+  for (;;) {
+    bool run = p >= 0;
+    if (run) {
+      const int g = p / S;
+      const float rho = per(g)[L::oRho];
+      const float* kg = kin(g);
+      const float* Gg = per(g) + L::oG;
+      const int chunk = min(check, cfg.iters - it);
+#pragma unroll 1
+      for (int k = 0; k < chunk; ++k) {
+        if (CONE == CONE_SOC) admm_iteration_soc<M>(y, w, mq, kg, cfg, rho);
+        else admm_iteration<M>(y, w, mq, kg, cfg, rho);
+      }
+      it += chunk;
+      // residuals from the parked copy: computed from registers, they would
+      // need more than the 168 a thread has next to the iterate
+      float rp, rd;
+      park_store(threadIdx.x);
+      {
+        const float* rec = park + threadIdx.x * L::PW;
+        if (CONE == CONE_SOC) admm_residuals_soc<M>(rec, rec + L::pW, rec + L::pM, Gg, cfg, rho, rp, rd);
+        else admm_residuals<M>(rec, rec + L::pW, rec + L::pM, Gg, cfg, rho, rp, rd);
+      }
+      park_load(threadIdx.x);
+      const bool conv = cfg.eps > 0.f && rp <= cfg.eps && rd <= cfg.eps;
+      if (conv || it >= cfg.iters) {
+        finish(p, rp, rd, conv);
+        run = false;
+      }
+      // residual balancing (OSQP, Stellato et al. 2020, Sec. 5.2): each
+      // running QP proposes log sqrt(r_p / r_d) for its grasp; 0 once stopped
+      if (adaptive) per(g)[L::oVote + p % S] = run ? 0.5f * __logf(fmaxf(rp, 1e-12f) / fmaxf(rd, 1e-12f)) : 0.f;
+      if (!run) p = -1;
+    }
+    const int n_run = __syncthreads_count(run);
+    if (n_run == 0) break;
+    if (adaptive) {
+      // one decision per grasp: rho moves by the geometric mean of its running
+      // QPs' proposals when that is more than 5x (clamped to [1e-6, 1e6])
+      bool moved = false;
+      if (role && lane == 0) {
+        float* pg = per(gl);
+        float sh = 0.f;
+        int cnt = 0;
+        for (int j = 0; j < S; ++j) {
+          const float v = pg[L::oVote + j];
+          sh += v;
+          cnt += v != 0.f;
+        }
+        const float cur = pg[L::oRho];
+        float nxt = cur;
+        if (cnt > 0 && fabsf(sh / cnt) > 1.6094379f)  // log 5
+          nxt = fminf(fmaxf(cur * __expf(sh / cnt), 1e-6f), 1e6f);
+        pg[L::oRho + 1] = cur;
+        pg[L::oRho] = nxt;
+        moved = nxt != cur;
+      }
+      if (!__syncthreads_or(moved)) goto repack;  // no grasp of the CTA changed rho
+      const bool mine = p >= 0;
+      if (mine) {  // re-express the iterate at the grasp's new rho, then park it (its registers go to the setup)
+        const float* pg = per(p / S);
+        if (pg[L::oRho] != pg[L::oRho + 1]) rescale_w<M, CONE>(w, pg[L::oRho + 1] / pg[L::oRho], cfg);
+        park_store(threadIdx.x);
+      }
+      AdmmCfg cl = cfg;
+      bool upd = false;
+      if (role) {
+        cl.rho = per(gl)[L::oRho];
+        upd = cl.rho != per(gl)[L::oRho + 1];
+      }
+      setup_kinv<M>(upd, lane, S, per(gl) + L::oG, per(gl) + L::oK, kin(gl), cl);  // barriers inside
+      if (mine) park_load(threadIdx.x);
+    }
+  repack:
+    if ((n_run + 31) / 32 < warps) {
+      // repack: running QPs, in thread order, to threads 0 .. n_run - 1
+      const unsigned bal = __ballot_sync(wmask, p >= 0);
+      if (wl == 0) wcount[warp] = __popc(bal);
+      __syncthreads();
+      if (p >= 0) {
+        int r = __popc(bal & ((1u << wl) - 1u));
+        for (int k = 0; k < warp; ++k) r += wcount[k];
+        park_store(r);
+      }
+      __syncthreads();
+      p = -1;
+      if ((int)threadIdx.x < n_run) park_load(threadIdx.x);
+      warps = (n_run + 31) / 32;
+    }
   }
-  float rp, rd;
-  bool conv;
-  AdmmCfg cl = cfg;  // this grasp's penalty may move
-  int it;
-  if (adaptive) {
-    auto setup = [&](bool upd, const AdmmCfg& cc) { setup_kinv<M>(upd, lane, S, Gs, per + L::oK, kin, cc); };
-    it = admm_solve_adaptive<M, CONE>(active, lane, S, y, w, mq, kin, Gs, cl, per + L::oQ, setup, rp, rd, conv);
-    if (!active) return;  // no barriers below
-  } else {
-    it = admm_solve<M, CONE>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
-  }
-  float Q = 0.f;
-  bool fin = true;
-#pragma unroll
-  for (int r = 0; r < 6; ++r) {
-    float s = cfg.beta * t[r];
-#pragma unroll
-    for (int a = 0; a < NV; ++a) s = fmaf(-Gs[r * NV + a], y[a], s);
-    Q = fmaf(s, s, Q);
-  }
-#pragma unroll
-  for (int a = 0; a < NV; ++a) {
-    yio[q * NV + a] = y[a];
-    fin = fin && isfinite(y[a]);
-    Q = fmaf(cfg.eps_reg * y[a], y[a], Q);  // regularised value when eps_reg > 0
-  }
-#pragma unroll
-  for (int r = 0; r < NC; ++r) {
-    const float p = CONE == CONE_SOC ? proj_row_soc<M>(w, r, cfg.gamma) : proj_row<M>(w[r], r, cfg.gamma);
-    zio[q * NC + r] = p;
-    lio[q * NC + r] = cl.rho * (w[r] - p);
-  }
-  Qout[q] = Q;
-  if (iters_out) iters_out[q] = it;
-  if (res_out) {
-    res_out[2 * q] = rp;
-    res_out[2 * q + 1] = rd;
-  }
-  int st = *stat;
-  if (!fin || !isfinite(Q)) st |= BODEX_ST_NONFINITE;
-  if (cfg.eps > 0.f && !conv) st |= BODEX_ST_NOT_CONVERGED;
-  if (status_out) status_out[q] = st;
 }
 
 // ============================================================================ kernel: fused evaluation / step
@@ -644,6 +791,16 @@ inline int gpb_for(int s) {
   return std::max(1, std::min(CTA_LANES / s, (int)fit));
 }
 
+// Grasps per CTA of the batched QP kernel: 96 lanes / s, capped by its
+// shared memory.
+template <int M, int CONE>
+inline int qp_gpb(int s) {
+  constexpr size_t kMaxSmem = 227 * 1024;
+  using L = LayQP<M, CONE>;
+  const size_t per = 4u * (size_t)(L::KS + L::PER + s * L::PW);
+  return std::max(1, std::min(CTA_LANES / s, (int)((kMaxSmem - 128) / per)));
+}
+
 // Grasps per CTA: the requested count (autotuner), else the default,
 // never more than fit in 96 lanes and in shared memory.
 template <int M>
@@ -712,8 +869,8 @@ template <int M>
 inline int run_qp(const float* G, int B, const float* T, int s, const AdmmCfg& cfg, int warm, float* y, float* z,
            float* lam, float* Q, int32_t* iters, int32_t* status, float* res, cudaStream_t st) {
   if (B == 0) return BODEX_OK;
-  const int gpb = gpb_for<M>(s);
-  const size_t bytes = Lay<M>::bytes(gpb);
+  const int gpb = cfg.cone ? qp_gpb<M, CONE_SOC>(s) : qp_gpb<M, CONE_PYR>(s);
+  const size_t bytes = cfg.cone ? LayQP<M, CONE_SOC>::bytes(gpb, s) : LayQP<M, CONE_PYR>::bytes(gpb, s);
   if (cfg.cone) {
     if (int r = ensure_smem(qp_solve_kernel<M, CONE_SOC>, bytes)) return r;
     qp_solve_kernel<M, CONE_SOC><<<(B + gpb - 1) / gpb, gpb * s, bytes, st>>>(G, B, T, s, cfg, warm, y, z, lam, Q,

@@ -1,0 +1,38 @@
+"""The batched QP kernel repacks the QPs still running into the lowest warps
+of the CTA at every residual check.  A QP's arithmetic must not depend on
+which thread runs it: results are bitwise those of the same QP in another
+batch (other CTA neighbours, so other repacking), with fixed and with
+adaptive rho, and with a wrench count that leaves the last warp partial."""
+import numpy as np
+import pytest
+
+from gpu_helpers import I, O, cuda, host, torch
+
+import paper_2412_16490_gb300 as bx
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("s", [12, 7])
+@pytest.mark.parametrize("adaptive", [0, 1])
+def test_qp_results_do_not_depend_on_the_batch(s, adaptive):
+    T = cuda(I.wrench_set(12)[:s].copy())
+    p, n = I.random_contacts(50, 5, seed=95)
+    G = cuda(O.grasp_matrix(p, n).astype(np.float32))
+    prm = bx.qp_params(eps_abs=1e-5, max_iter=3000, check_every=10, adaptive_rho=adaptive)
+    full = bx.bodex_qp_solve_batch(G, T, prm)
+    sub = bx.bodex_qp_solve_batch(G[3:41].contiguous(), T, prm)  # every grasp in another CTA position
+    for k in ("y", "z", "lam", "Q", "iters", "status", "res"):
+        assert torch.equal(full[k][3:41], sub[k]), k
+    it = host(full["iters"])
+    assert it.min() * 3 < it.max()  # iteration counts spread widely: QPs stop at different checks
+
+
+def test_fixed_iteration_batch_runs_every_qp_to_the_cap():
+    T = cuda(I.wrench_set(12))
+    p, n = I.random_contacts(17, 4, seed=96)
+    G = cuda(O.grasp_matrix(p, n).astype(np.float32))
+    out = bx.bodex_qp_solve_batch(G, T, bx.qp_params(max_iter=37))
+    assert (host(out["iters"]) == 37).all()
+    assert (host(out["status"]) == 0).all()
+    assert np.isfinite(host(out["Q"])).all() and (host(out["res"]) >= 0).all()

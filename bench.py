@@ -37,7 +37,7 @@ SM_COUNT, FP32_LANES = 152, 128
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused_kernel<5, step> launch on this
 # workload (profiles/fused_step_paper_4096.md; a 5-step launch of the same kernel -- the state
 # is read once per launch and the grid stays in L2, so the bytes do not grow with the steps)
-TRAFFIC_BYTES = 14_556_928 + 5_888
+TRAFFIC_BYTES = 14_551_552 + 1_280
 TRAFFIC_SOURCE = "ncu capture in profiles/fused_step_paper_4096.md (5-step launch; per-launch bytes)"
 
 
@@ -214,6 +214,11 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
 
     n_up = args.upper_steps
+    if args.qp_only:  # the standalone batched QPs alone (a small command for profiler captures)
+        line = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev)
+        if rank == 0:
+            print(json.dumps(dict(line, workload="49152 cold-start QPs at the paper geometry, to 1e-5, cap 5000")))
+        return
 
     def one_run():
         st.set_pose(x_dev)
@@ -267,12 +272,11 @@ def run_ours(args, rank, world, local_rank):
         extra["admm_sweep"] = admm_sweep(bx, torch, H, Ob, x_dev, T_dev, P, B)
         extra["synthesis"] = synthesis_rate(bx, torch, H, Ob, x_dev, T_dev, sp)
         extra["energies"] = energy_variants(bx, torch, H, Ob, x_dev, T_dev, P)
-        # the pyramid's QPs with the adaptive penalty (faster here); fixed rho beside it
-        extra["qp_solves"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev, adaptive_rho=1)
-        extra["qp_solves"]["adaptive_rho"] = True
-        extra["qp_solves"]["fixed_rho"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev)
+        # the pyramid's QPs with the default fixed penalty; adaptive rho beside it
+        extra["qp_solves"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev)
+        extra["qp_solves"]["adaptive_rho"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev, adaptive_rho=1)
         extra["qp_solves_elliptic_cone"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev, cone=bx.CONE_ELLIPTIC)
-        extra["qp_solves_warm_in_loop"] = qp_solve_rate_warm(bx, torch, H, Ob, x_dev, T_dev, P)
+        extra["qp_solves_warm_in_loop"] = qp_solve_rate_warm(bx, torch, H, Ob, x_dev, T_dev, P, adaptive_rho=0)
         extra["e2e"] = e2e_rate(bx, torch, H, Ob, st, x0, T_dev, sp)
         extra["persistent_mixed"] = persistent_mixed(bx, torch, P)
         if args.serve_jobs > 0:
@@ -396,7 +400,9 @@ def persistent_mixed(bx, torch, P):
     ms_res_plain = _timed(torch, plain_res, reps=2)
     big = max(J, key=lambda j: j["x0"].shape[0])
     t0 = time.perf_counter()
-    tuned = autotune(big["hand"], big["obj"], big["x0"][:2048].contiguous(), Tt, P, steps=N_STEPS)
+    # tuned on the largest job at its full size: the best CTA tile depends on
+    # how many CTAs the launch spreads over the SMs, so a small sample misleads
+    tuned = autotune(big["hand"], big["obj"], big["x0"], Tt, P, steps=N_STEPS)
     tune_s = time.perf_counter() - t0
     ms_tuned = _timed(torch, lambda: persistent(tuned_params(tuned, P)))
     res = torch.cat([j["state"].residual() for j in J])
@@ -559,9 +565,26 @@ def qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev, cone=0, adaptive_rho=0):
     dt = a.elapsed_time(b) / 1e3
     conv = ((out["status"] & bx.ST_NOT_CONVERGED) == 0)
     it = out["iters"].float()
+    # algorithmic FLOPs of the iterations actually executed (F_it per QP-iteration)
+    m = int(G.shape[2]) // 3
+    f_it = qp_iteration_flops(m, cone)
+    tflops = float(it.sum().item()) * f_it / dt / 1e12
+    peak = fp32_peak_tflops((measured_peaks() or {}).get("sm_max_mhz") or 2070.0)
     return {"value": float(conv.sum().item()) / dt, "unit": "QP solves/s (converged to 1e-5)",
             "qps": int(conv.numel()), "converged_frac": float(conv.float().mean().item()),
-            "iters_median": float(it.median().item()), "iters_max": int(it.max().item()), "ms": dt * 1e3}
+            "iters_median": float(it.median().item()), "iters_mean": float(it.mean().item()),
+            "iters_max": int(it.max().item()), "ms": dt * 1e3,
+            "roofline": {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
+                         "flops_per_qp_iteration": f_it}}
+
+
+def qp_iteration_flops(m, cone=0):
+    """F_it of one ADMM iteration: admm_iter_flops for the pyramid; the
+    elliptic cone's A has nnz(A) = 5m and nc = 4m + 1 rows."""
+    if not cone:
+        return admm_iter_flops(m)
+    nv, nc, nnz = 3 * m, 4 * m + 1, 5 * m
+    return 4 * nnz + 2 * nv * nv + 6 * nv + 10 * nc
 
 
 def qp_solve_rate_warm(bx, torch, H, Ob, x_dev, T_dev, P, adaptive_rho=1, at_step=100):
@@ -640,6 +663,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--quick", action="store_true", help="skip the QP and e2e side measurements")
     ap.add_argument("--serve-jobs", type=int, default=300, help="jobs in the serving measurement (0 skips it)")
+    ap.add_argument("--qp-only", action="store_true", help="only the standalone QP measurement (profiler captures)")
     ap.add_argument("--upper-steps", type=int, default=N_STEPS,
                     help="upper iterations per run (200 for the bench line; fewer for profiler captures)")
     args = ap.parse_args()

@@ -644,6 +644,39 @@ __device__ __forceinline__ void At_contact(float v0, const float (&vk)[8], float
   ge = fmaf(S8, (vk[0] + vk[3]) - (vk[4] + vk[7]), C8 * ((vk[1] + vk[2]) - (vk[5] + vk[6])));
 }
 
+// Per-contact pieces of one ADMM iteration.  admm_iteration and the
+// several-lanes-per-QP form of the batched QP kernel are both written with
+// them, so the two give bitwise equal iterates.
+// rhs of contact i's three components: sigma y - q + rho A_i^T v with
+// v = 2 Pi(w) - w; vsum is the sum row's entry of v.
+__device__ __forceinline__ void pyr_contact_rhs(const float* wi, float vsum, const float* yi, const float* mqi,
+                                                const AdmmCfg& c, float rho, float* rhs) {
+  const float v0 = fmaf(2.f, fminf(fmaxf(wi[0], 0.f), 1.f), -wi[0]) + vsum;
+  // facet rows (bounds (-inf, 0]): 2 min(w, 0) - w is exactly -|w|, which
+  // the hardware applies as a free operand modifier
+  float vk[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) vk[k] = -fabsf(wi[1 + k]);
+  float gn, gd, ge;
+  At_contact(v0, vk, c.mu_c8, gn, gd, ge);
+  rhs[0] = fmaf(c.sigma, yi[0], fmaf(rho, gn, mqi[0]));
+  rhs[1] = fmaf(c.sigma, yi[1], fmaf(rho, gd, mqi[1]));
+  rhs[2] = fmaf(c.sigma, yi[2], fmaf(rho, ge, mqi[2]));
+}
+
+// Contact i's nine rows: w <- (w + A_i yt) - alpha Pi(w); (tn, td, te) is
+// the contact's part of yt.
+__device__ __forceinline__ void pyr_contact_update(float* wi, float tn, float td, float te, const AdmmCfg& c) {
+  const float al = c.alpha;
+  wi[0] = fmaf(-al, __saturatef(wi[0]), wi[0] + tn);
+  const float base = -c.mu_c8 * tn;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float zt = fmaf(kFC[k], td, fmaf(kFS[k], te, base));
+    wi[1 + k] = fmaf(-al, fminf(wi[1 + k], 0.f), wi[1 + k] + zt);
+  }
+}
+
 template <int M>
 __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* mq, const float* Kinv,
                                                const AdmmCfg& c, float rho) {
@@ -652,19 +685,7 @@ __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* 
   float rhs[NV];
   const float vsum = fmaf(2.f, fmaxf(w[9 * M], c.gamma), -w[9 * M]);
 #pragma unroll
-  for (int i = 0; i < M; ++i) {
-    const float v0 = fmaf(2.f, fminf(fmaxf(w[9 * i], 0.f), 1.f), -w[9 * i]) + vsum;
-    // facet rows (bounds (-inf, 0]): 2 min(w, 0) - w is exactly -|w|, which
-    // the hardware applies as a free operand modifier
-    float vk[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) vk[k] = -fabsf(w[9 * i + 1 + k]);
-    float gn, gd, ge;
-    At_contact(v0, vk, c.mu_c8, gn, gd, ge);
-    rhs[3 * i] = fmaf(c.sigma, y[3 * i], fmaf(rho, gn, mq[3 * i]));
-    rhs[3 * i + 1] = fmaf(c.sigma, y[3 * i + 1], fmaf(rho, gd, mq[3 * i + 1]));
-    rhs[3 * i + 2] = fmaf(c.sigma, y[3 * i + 2], fmaf(rho, ge, mq[3 * i + 2]));
-  }
+  for (int i = 0; i < M; ++i) pyr_contact_rhs(w + 9 * i, vsum, y + 3 * i, mq + 3 * i, c, rho, rhs + 3 * i);
   // yt = alpha K^-1 rhs from the packed upper triangle, column by column:
   // entry (a, b), a <= b, adds K_ab rhs_b to yt_a and, off the diagonal,
   // K_ab rhs_a to yt_b.  The loops unroll completely (every index is a
@@ -689,43 +710,59 @@ __device__ __forceinline__ void admm_iteration(float* y, float* w, const float* 
   float sumn = 0.f;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
-    float* wi = w + 9 * i;
-    const float tn = yt[3 * i], td = yt[3 * i + 1], te = yt[3 * i + 2];
-    sumn += tn;
-    wi[0] = fmaf(-al, __saturatef(wi[0]), wi[0] + tn);
-    const float base = -c.mu_c8 * tn;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const float zt = fmaf(kFC[k], td, fmaf(kFS[k], te, base));
-      wi[1 + k] = fmaf(-al, fminf(wi[1 + k], 0.f), wi[1 + k] + zt);
-    }
+    sumn += yt[3 * i];
+    pyr_contact_update(w + 9 * i, yt[3 * i], yt[3 * i + 1], yt[3 * i + 2], c);
   }
   w[9 * M] = fmaf(-al, fmaxf(w[9 * M], c.gamma), w[9 * M] + sumn);
 #pragma unroll
   for (int a = 0; a < NV; ++a) y[a] = fmaf(bl, y[a], yt[a]);
 }
 
-// Infinity-norm residuals at (y, w): primal |A y - z|, dual |P y + q + A^T lam|,
-// z = Pi(w), lam = rho (w - Pi(w)).
-template <int M>
-__device__ inline void admm_residuals(const float* y, const float* w, const float* mq, const float* G,
-                                      const AdmmCfg& c, float rho, float& rp, float& rd) {
-  constexpr int NV = Admm<M>::NV;
-  rp = 0.f;
-  float sumn = 0.f;
+// Per-contact pieces of the residuals, shared by admm_residuals and the
+// wide form of the batched QP kernel (the maxima do not depend on the order
+// in which rows are visited, and every sum is formed in the same order).
+// Primal rows of contact i: rp = max(rp, |A_i y - Pi(w_i)|).
+template <bool SCALES>
+__device__ __forceinline__ void pyr_contact_primal(const float* wi, float yn, float yd, float ye, const AdmmCfg& c,
+                                                   float& rp, float& nprim) {
+  const float p0 = fminf(fmaxf(wi[0], 0.f), 1.f);
+  rp = fmaxf(rp, fabsf(yn - p0));
+  if constexpr (SCALES) nprim = fmaxf(nprim, fmaxf(fabsf(yn), fabsf(p0)));
 #pragma unroll
-  for (int i = 0; i < M; ++i) {
-    const float yn = y[3 * i], yd = y[3 * i + 1], ye = y[3 * i + 2];
-    sumn += yn;
-    rp = fmaxf(rp, fabsf(yn - fminf(fmaxf(w[9 * i], 0.f), 1.f)));
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      const float ay = fmaf(kFC[k], yd, fmaf(kFS[k], ye, -c.mu_c8 * yn));
-      rp = fmaxf(rp, fabsf(ay - fminf(w[9 * i + 1 + k], 0.f)));
-    }
+  for (int k = 0; k < 8; ++k) {
+    const float ay = fmaf(kFC[k], yd, fmaf(kFS[k], ye, -c.mu_c8 * yn));
+    const float pk = fminf(wi[1 + k], 0.f);
+    rp = fmaxf(rp, fabsf(ay - pk));
+    if constexpr (SCALES) nprim = fmaxf(nprim, fmaxf(fabsf(ay), fabsf(pk)));
   }
-  rp = fmaxf(rp, fabsf(sumn - fmaxf(w[9 * M], c.gamma)));
-  float gy[6];
+}
+
+// Contact i's three components of A^T d, d = w - Pi(w) (dsum: the sum row's d).
+__device__ __forceinline__ void pyr_contact_atd(const float* wi, float dsum, const AdmmCfg& c, float* at) {
+  const float d0 = (wi[0] - fminf(fmaxf(wi[0], 0.f), 1.f)) + dsum;
+  float dk[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) dk[k] = wi[1 + k] - fminf(wi[1 + k], 0.f);
+  At_contact(d0, dk, c.mu_c8, at[0], at[1], at[2]);
+}
+
+// Dual residual of component a: rd = max(rd, |rho (A^T d)_a + (P y)_a + q_a|)
+// with P y = 2 G^T (G y) + 2 eps y; gy = G y.  A^T lam = rho A^T d: the sums
+// run on d and rho enters once, in an explicit fmaf.
+template <int NV, bool SCALES>
+__device__ __forceinline__ void dual_component(const float* G, int a, const float* gy, float ya, float mqa, float at,
+                                               const AdmmCfg& c, float rho, float& rd, float& ndual) {
+  float s = 0.f;
+#pragma unroll
+  for (int r = 0; r < 6; ++r) s = fmaf(lds32(G + r * NV + a), gy[r], s);
+  const float py = fmaf(2.f * c.eps_reg, ya, 2.f * s);
+  rd = fmaxf(rd, fabsf(fmaf(rho, at, py - mqa)));
+  if constexpr (SCALES) ndual = fmaxf(ndual, fmaxf(fabsf(py), fmaxf(fabsf(rho * at), fabsf(mqa))));
+}
+
+// gy = G y (6 x nv, row-major in shared memory), each row summed in column order.
+template <int NV>
+__device__ __forceinline__ void g_times(const float* G, const float* y, float* gy) {
 #pragma unroll
   for (int r = 0; r < 6; ++r) {
     float s = 0.f;
@@ -733,25 +770,42 @@ __device__ inline void admm_residuals(const float* y, const float* w, const floa
     for (int a = 0; a < NV; ++a) s = fmaf(lds32(G + r * NV + a), y[a], s);
     gy[r] = s;
   }
-  const float lsum = rho * (w[9 * M] - fmaxf(w[9 * M], c.gamma));
-  rd = 0.f;
+}
+
+// Infinity-norm residuals at (y, w): primal |A y - z|, dual |P y + q + A^T lam|,
+// z = Pi(w), lam = rho (w - Pi(w)).  With SCALES, also the magnitudes that
+// normalise them (OSQP, Stellato et al. 2020, Sec. 5.2):
+// scale[0] = max(|A y|, |z|), scale[1] = max(|P y|, |A^T lam|, |q|).
+template <int M, bool SCALES = false>
+__device__ inline void admm_residuals(const float* y, const float* w, const float* mq, const float* G,
+                                      const AdmmCfg& c, float rho, float& rp, float& rd, float* scale = nullptr) {
+  constexpr int NV = Admm<M>::NV;
+  rp = 0.f;
+  float sumn = 0.f, nprim = 0.f;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
-    const float l0 = fmaf(rho, w[9 * i] - fminf(fmaxf(w[9 * i], 0.f), 1.f), lsum);
-    float lk[8];
+    sumn += y[3 * i];
+    pyr_contact_primal<SCALES>(w + 9 * i, y[3 * i], y[3 * i + 1], y[3 * i + 2], c, rp, nprim);
+  }
+  const float psum = fmaxf(w[9 * M], c.gamma);
+  rp = fmaxf(rp, fabsf(sumn - psum));
+  if constexpr (SCALES) nprim = fmaxf(nprim, fmaxf(fabsf(sumn), fabsf(psum)));
+  float gy[6];
+  g_times<NV>(G, y, gy);
+  const float dsum = w[9 * M] - psum;
+  rd = 0.f;
+  float ndual = 0.f;
 #pragma unroll
-    for (int k = 0; k < 8; ++k) lk[k] = rho * (w[9 * i + 1 + k] - fminf(w[9 * i + 1 + k], 0.f));
+  for (int i = 0; i < M; ++i) {
     float at[3];
-    At_contact(l0, lk, c.mu_c8, at[0], at[1], at[2]);
+    pyr_contact_atd(w + 9 * i, dsum, c, at);
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int a = 3 * i + q;
-      float s = 0.f;
-#pragma unroll
-      for (int r = 0; r < 6; ++r) s = fmaf(lds32(G + r * NV + a), gy[r], s);
-      const float py = fmaf(2.f * c.eps_reg, y[a], 2.f * s);
-      rd = fmaxf(rd, fabsf(py - mq[a] + at[q]));
-    }
+    for (int q = 0; q < 3; ++q)
+      dual_component<NV, SCALES>(G, 3 * i + q, gy, y[3 * i + q], mq[3 * i + q], at[q], c, rho, rd, ndual);
+  }
+  if constexpr (SCALES) {
+    scale[0] = nprim;
+    scale[1] = ndual;
   }
 }
 
@@ -794,6 +848,29 @@ __device__ __forceinline__ void proj_soc(float s, float u1, float u2, float& ps,
   }
 }
 
+// Per-contact pieces of the elliptic-cone iteration (as pyr_contact_rhs /
+// pyr_contact_update): rhs of contact i, keeping pc = Pi of its cone rows
+// for the update.
+__device__ __forceinline__ void soc_contact_rhs(const float* wi, float vsum, const float* yi, const float* mqi,
+                                                const AdmmCfg& c, float rho, float* rhs, float* pc) {
+  proj_soc(wi[1], wi[2], wi[3], pc[0], pc[1], pc[2]);
+  const float v0 = fmaf(2.f, __saturatef(wi[0]), -wi[0]) + vsum;
+  const float gn = fmaf(c.mu, fmaf(2.f, pc[0], -wi[1]), v0);
+  const float gd = fmaf(2.f, pc[1], -wi[2]), ge = fmaf(2.f, pc[2], -wi[3]);
+  rhs[0] = fmaf(c.sigma, yi[0], fmaf(rho, gn, mqi[0]));
+  rhs[1] = fmaf(c.sigma, yi[1], fmaf(rho, gd, mqi[1]));
+  rhs[2] = fmaf(c.sigma, yi[2], fmaf(rho, ge, mqi[2]));
+}
+
+__device__ __forceinline__ void soc_contact_update(float* wi, const float* pc, float tn, float td, float te,
+                                                   const AdmmCfg& c) {
+  const float al = c.alpha;
+  wi[0] = fmaf(-al, __saturatef(wi[0]), wi[0] + tn);
+  wi[1] = fmaf(-al, pc[0], fmaf(c.mu, tn, wi[1]));
+  wi[2] = fmaf(-al, pc[1], wi[2] + td);
+  wi[3] = fmaf(-al, pc[2], wi[3] + te);
+}
+
 template <int M>
 __device__ __forceinline__ void admm_iteration_soc(float* y, float* w, const float* mq, const float* Kinv,
                                                    const AdmmCfg& c, float rho) {
@@ -802,16 +879,7 @@ __device__ __forceinline__ void admm_iteration_soc(float* y, float* w, const flo
   float rhs[NV], pc[3 * M];
   const float vsum = fmaf(2.f, fmaxf(w[4 * M], c.gamma), -w[4 * M]);
 #pragma unroll
-  for (int i = 0; i < M; ++i) {
-    const float* wi = w + 4 * i;
-    proj_soc(wi[1], wi[2], wi[3], pc[3 * i], pc[3 * i + 1], pc[3 * i + 2]);
-    const float v0 = fmaf(2.f, __saturatef(wi[0]), -wi[0]) + vsum;
-    const float gn = fmaf(c.mu, fmaf(2.f, pc[3 * i], -wi[1]), v0);
-    const float gd = fmaf(2.f, pc[3 * i + 1], -wi[2]), ge = fmaf(2.f, pc[3 * i + 2], -wi[3]);
-    rhs[3 * i] = fmaf(c.sigma, y[3 * i], fmaf(rho, gn, mq[3 * i]));
-    rhs[3 * i + 1] = fmaf(c.sigma, y[3 * i + 1], fmaf(rho, gd, mq[3 * i + 1]));
-    rhs[3 * i + 2] = fmaf(c.sigma, y[3 * i + 2], fmaf(rho, ge, mq[3 * i + 2]));
-  }
+  for (int i = 0; i < M; ++i) soc_contact_rhs(w + 4 * i, vsum, y + 3 * i, mq + 3 * i, c, rho, rhs + 3 * i, pc + 3 * i);
   // yt = alpha K^-1 rhs (packed upper triangle, column order as in admm_iteration)
   float yt[NV];
 #pragma unroll
@@ -830,66 +898,66 @@ __device__ __forceinline__ void admm_iteration_soc(float* y, float* w, const flo
   float sumn = 0.f;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
-    float* wi = w + 4 * i;
-    const float tn = yt[3 * i], td = yt[3 * i + 1], te = yt[3 * i + 2];
-    sumn += tn;
-    wi[0] = fmaf(-al, __saturatef(wi[0]), wi[0] + tn);
-    wi[1] = fmaf(-al, pc[3 * i], fmaf(c.mu, tn, wi[1]));
-    wi[2] = fmaf(-al, pc[3 * i + 1], wi[2] + td);
-    wi[3] = fmaf(-al, pc[3 * i + 2], wi[3] + te);
+    sumn += yt[3 * i];
+    soc_contact_update(w + 4 * i, pc + 3 * i, yt[3 * i], yt[3 * i + 1], yt[3 * i + 2], c);
   }
   w[4 * M] = fmaf(-al, fmaxf(w[4 * M], c.gamma), w[4 * M] + sumn);
 #pragma unroll
   for (int a = 0; a < NV; ++a) y[a] = fmaf(bl, y[a], yt[a]);
 }
 
-template <int M>
+// Primal rows of contact i of the elliptic cone, and d = w - Pi(w) of its
+// four rows (per-contact piece of admm_residuals_soc, as pyr_contact_primal).
+template <bool SCALES>
+__device__ __forceinline__ void soc_contact_primal(const float* wi, float yn, float yd, float ye, const AdmmCfg& c,
+                                                   float& rp, float& nprim, float* dl) {
+  const float p0 = __saturatef(wi[0]);
+  float ps, p1, p2;
+  proj_soc(wi[1], wi[2], wi[3], ps, p1, p2);
+  rp = fmaxf(rp, fabsf(yn - p0));
+  rp = fmaxf(rp, fabsf(fmaf(c.mu, yn, -ps)));
+  rp = fmaxf(rp, fabsf(yd - p1));
+  rp = fmaxf(rp, fabsf(ye - p2));
+  if constexpr (SCALES)
+    nprim = fmaxf(fmaxf(nprim, fmaxf(fabsf(yn), fabsf(c.mu * yn))),
+                  fmaxf(fmaxf(fabsf(yd), fabsf(ye)), fmaxf(fmaxf(fabsf(p0), fabsf(ps)), fmaxf(fabsf(p1), fabsf(p2)))));
+  dl[0] = wi[0] - p0;
+  dl[1] = wi[1] - ps;
+  dl[2] = wi[2] - p1;
+  dl[3] = wi[3] - p2;
+}
+
+template <int M, bool SCALES = false>
 __device__ inline void admm_residuals_soc(const float* y, const float* w, const float* mq, const float* G,
-                                          const AdmmCfg& c, float rho, float& rp, float& rd) {
+                                          const AdmmCfg& c, float rho, float& rp, float& rd,
+                                          float* scale = nullptr) {
   constexpr int NV = Admm<M>::NV;
   rp = 0.f;
-  float sumn = 0.f;
-  float lam[4 * M];
+  float sumn = 0.f, nprim = 0.f;
+  float dl[4 * M];  // d = w - Pi(w); lam = rho d
 #pragma unroll
   for (int i = 0; i < M; ++i) {
-    const float* wi = w + 4 * i;
-    const float yn = y[3 * i], yd = y[3 * i + 1], ye = y[3 * i + 2];
-    sumn += yn;
-    const float p0 = __saturatef(wi[0]);
-    float ps, p1, p2;
-    proj_soc(wi[1], wi[2], wi[3], ps, p1, p2);
-    rp = fmaxf(rp, fabsf(yn - p0));
-    rp = fmaxf(rp, fabsf(fmaf(c.mu, yn, -ps)));
-    rp = fmaxf(rp, fabsf(yd - p1));
-    rp = fmaxf(rp, fabsf(ye - p2));
-    lam[4 * i] = rho * (wi[0] - p0);
-    lam[4 * i + 1] = rho * (wi[1] - ps);
-    lam[4 * i + 2] = rho * (wi[2] - p1);
-    lam[4 * i + 3] = rho * (wi[3] - p2);
+    sumn += y[3 * i];
+    soc_contact_primal<SCALES>(w + 4 * i, y[3 * i], y[3 * i + 1], y[3 * i + 2], c, rp, nprim, dl + 4 * i);
   }
-  rp = fmaxf(rp, fabsf(sumn - fmaxf(w[4 * M], c.gamma)));
-  const float lsum = rho * (w[4 * M] - fmaxf(w[4 * M], c.gamma));
+  const float psum = fmaxf(w[4 * M], c.gamma);
+  rp = fmaxf(rp, fabsf(sumn - psum));
+  if constexpr (SCALES) nprim = fmaxf(nprim, fmaxf(fabsf(sumn), fabsf(psum)));
+  const float dsum = w[4 * M] - psum;
+  float ndual = 0.f;
   float gy[6];
-#pragma unroll
-  for (int r = 0; r < 6; ++r) {
-    float s = 0.f;
-#pragma unroll
-    for (int a = 0; a < NV; ++a) s = fmaf(lds32(G + r * NV + a), y[a], s);
-    gy[r] = s;
-  }
+  g_times<NV>(G, y, gy);
   rd = 0.f;
 #pragma unroll
   for (int i = 0; i < M; ++i) {
-    const float at[3] = {fmaf(c.mu, lam[4 * i + 1], lam[4 * i]) + lsum, lam[4 * i + 2], lam[4 * i + 3]};
+    const float at[3] = {fmaf(c.mu, dl[4 * i + 1], dl[4 * i]) + dsum, dl[4 * i + 2], dl[4 * i + 3]};
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const int a = 3 * i + q;
-      float s = 0.f;
-#pragma unroll
-      for (int r = 0; r < 6; ++r) s = fmaf(lds32(G + r * NV + a), gy[r], s);
-      const float py = fmaf(2.f * c.eps_reg, y[a], 2.f * s);
-      rd = fmaxf(rd, fabsf(py - mq[a] + at[q]));
-    }
+    for (int q = 0; q < 3; ++q)
+      dual_component<NV, SCALES>(G, 3 * i + q, gy, y[3 * i + q], mq[3 * i + q], at[q], c, rho, rd, ndual);
+  }
+  if constexpr (SCALES) {
+    scale[0] = nprim;
+    scale[1] = ndual;
   }
 }
 
@@ -971,10 +1039,19 @@ __device__ inline void rescale_w(float* w, float ratio, const AdmmCfg& c) {
   }
 }
 
+// One QP's proposal for log(rho' / rho) in residual balancing (OSQP,
+// Stellato et al. 2020, Sec. 5.2): log sqrt((r_p / s_p) / (r_d / s_d)), each
+// residual relative to the magnitudes it is formed from (scale of
+// admm_residuals).  Unnormalised, a tiny absolute primal residual kept
+// pushing rho down to its floor, where the multipliers barely move.
+__device__ __forceinline__ float rho_vote(float rp, float rd, const float* scale) {
+  return 0.5f * __logf((fmaxf(rp, 1e-12f) * fmaxf(scale[1], 1e-12f)) / (fmaxf(rd, 1e-12f) * fmaxf(scale[0], 1e-12f)));
+}
+
 // ADMM to a residual target with the penalty adapted per grasp (the
 // residual-balancing rule of OSQP, Stellato et al. 2020, Sec. 5.2):
 // every `check` iterations each lane still running proposes
-// rho * sqrt(r_p / r_d); when the geometric mean of its grasp's proposals
+// rho * sqrt((r_p / s_p) / (r_d / s_d)) (rho_vote); when the geometric mean of its grasp's proposals
 // moves rho by more than 5x, the grasp re-expresses its iterates and rebuilds
 // K^-1 (all of its lanes share one K).  Lanes that converged stop iterating
 // but keep their grasp's rho.  Must be called by every thread of the CTA
@@ -988,6 +1065,7 @@ __device__ inline int admm_solve_adaptive(bool active, int lane, int S, float* y
   int it = 0;
   conv = !active;
   rp = rd = 0.f;
+  float scale[2] = {1.f, 1.f};
   const float tol = 1.6094379f;  // log 5
 #pragma unroll 1
   for (;;) {
@@ -999,13 +1077,13 @@ __device__ inline int admm_solve_adaptive(bool active, int lane, int S, float* y
         else admm_iteration<M>(y, w, mq, Kinv, c, c.rho);
       }
       it += chunk;
-      if (CONE == CONE_SOC) admm_residuals_soc<M>(y, w, mq, G, c, c.rho, rp, rd);
-      else admm_residuals<M>(y, w, mq, G, c, c.rho, rp, rd);
+      if (CONE == CONE_SOC) admm_residuals_soc<M, true>(y, w, mq, G, c, c.rho, rp, rd, scale);
+      else admm_residuals<M, true>(y, w, mq, G, c, c.rho, rp, rd, scale);
       conv = rp <= c.eps && rd <= c.eps;
     }
     const bool done = conv || it >= c.iters;
     if (__syncthreads_and(done)) break;
-    if (active) vote[lane] = done ? 0.f : 0.5f * __logf(fmaxf(rp, 1e-12f) / fmaxf(rd, 1e-12f));
+    if (active) vote[lane] = done ? 0.f : rho_vote(rp, rd, scale);
     __syncthreads();
     // every lane of a grasp reads the same votes in the same order: one decision per grasp
     float sh = 0.f;

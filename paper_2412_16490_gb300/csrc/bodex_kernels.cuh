@@ -125,6 +125,14 @@ __device__ inline void setup_kinv(bool active, int lane, int S, const float* Gs,
 // warp whose QPs all stopped waits at the barrier and issues nothing while
 // the others iterate.  A QP carries its iterate, -q, its iteration count and
 // its slot (grasp, wrench); K^-1, G and rho stay with the grasp.
+// The last QPs of a CTA (at most 32 / m per full warp) run in a wide form:
+// one QP per m lanes of a warp, lane i holding contact i's rows, the rhs exchanged by
+// warp shuffles and each lane forming three rows of alpha K^-1 rhs from a
+// dense copy of the grasp's K^-1.  An iteration then costs a few hundred
+// cycles of dependent latency instead of about a thousand, which is what
+// the slowest QPs of a batch run at.  Every multiply-add is the one-lane
+// form's, in the same order (row r of the product sums j = 0 .. nv-1 in
+// both), so the iterates agree bitwise.  Not used with adaptive rho.
 //
 // Shared memory: alpha K^-1 per grasp (stride as in the fused kernel), the
 // per-grasp block (G, Woodbury scratch, votes, rho), the parking area (one
@@ -144,6 +152,12 @@ struct LayQP {
   static constexpr int pW = align4(NV), pM = pW + align4(NC), pI = pM + align4(NV);
   static constexpr int PW0 = pI + 4;
   static constexpr int PW = (PW0 / 4) % 2 ? PW0 : PW0 + 4;
+  // wide form: QPs per warp, w rows per contact, dense K^-1 row stride
+  // (the dense row stride is an odd number of float4s, so that the lanes of
+  // a quarter-warp, which read different rows, hit distinct bank groups)
+  static constexpr int QPW = 32 / M, WPC = CONE == CONE_SOC ? 4 : 9;
+  static constexpr int NVP = (align4(NV) / 4) % 2 ? align4(NV) : align4(NV) + 4;
+  static constexpr int WIDE_PER_QP = PW + NV * NVP;  // a record and a dense K^-1 per wide QP
   static size_t bytes(int gpb, int s) { return 4u * ((size_t)gpb * (KS + PER) + (size_t)gpb * s * PW + 32); }
 };
 
@@ -261,6 +275,13 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
   const int nw = min(32, (int)blockDim.x - 32 * warp);
   const unsigned wmask = nw == 32 ? 0xffffffffu : (1u << nw) - 1u;  // this warp's threads
   int warps = (blockDim.x + 31) / 32;                                  // warps that hold running QPs
+  // warps that take wide groups (full warps that the parking area has room
+  // for), at most one: on the 49k-QP paper batch, groups in every warp of the
+  // CTA (up to 18 QPs at m = 5) took 3.05 ms against 2.68 ms with warp 0
+  // alone, the SMs turning issue-bound again
+  const int wide_warps = min(min(1, (int)blockDim.x / 32), GPB * S * L::PW / (L::QPW * L::WIDE_PER_QP));
+  const bool wide_ok = !adaptive && cfg.eps > 0.f && wide_warps > 0;
+  int n_run;
 #pragma unroll 1
   for (;;) {
     bool run = p >= 0;
@@ -278,12 +299,12 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
       it += chunk;
       // residuals from the parked copy: computed from registers, they would
       // need more than the 168 a thread has next to the iterate
-      float rp, rd;
+      float rp, rd, scale[2];
       park_store(threadIdx.x);
       {
         const float* rec = park + threadIdx.x * L::PW;
-        if (CONE == CONE_SOC) admm_residuals_soc<M>(rec, rec + L::pW, rec + L::pM, Gg, cfg, rho, rp, rd);
-        else admm_residuals<M>(rec, rec + L::pW, rec + L::pM, Gg, cfg, rho, rp, rd);
+        if (CONE == CONE_SOC) admm_residuals_soc<M, true>(rec, rec + L::pW, rec + L::pM, Gg, cfg, rho, rp, rd, scale);
+        else admm_residuals<M, true>(rec, rec + L::pW, rec + L::pM, Gg, cfg, rho, rp, rd, scale);
       }
       park_load(threadIdx.x);
       const bool conv = cfg.eps > 0.f && rp <= cfg.eps && rd <= cfg.eps;
@@ -292,11 +313,11 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
         run = false;
       }
       // residual balancing (OSQP, Stellato et al. 2020, Sec. 5.2): each
-      // running QP proposes log sqrt(r_p / r_d) for its grasp; 0 once stopped
-      if (adaptive) per(g)[L::oVote + p % S] = run ? 0.5f * __logf(fmaxf(rp, 1e-12f) / fmaxf(rd, 1e-12f)) : 0.f;
+      // running QP proposes rho_vote (normalised residuals) for its grasp; 0 once stopped
+      if (adaptive) per(g)[L::oVote + p % S] = run ? rho_vote(rp, rd, scale) : 0.f;
       if (!run) p = -1;
     }
-    const int n_run = __syncthreads_count(run);
+    n_run = __syncthreads_count(run);
     if (n_run == 0) break;
     if (adaptive) {
       // one decision per grasp: rho moves by the geometric mean of its running
@@ -336,6 +357,19 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
       if (mine) park_load(threadIdx.x);
     }
   repack:
+    if (wide_ok && n_run <= wide_warps * L::QPW) {
+      // to the wide form: the running QPs parked in thread order (record r)
+      const unsigned bal = __ballot_sync(wmask, p >= 0);
+      if (wl == 0) wcount[warp] = __popc(bal);
+      __syncthreads();
+      if (p >= 0) {
+        int r = __popc(bal & ((1u << wl) - 1u));
+        for (int k = 0; k < warp; ++k) r += wcount[k];
+        park_store(r);
+      }
+      __syncthreads();
+      break;
+    }
     if ((n_run + 31) / 32 < warps) {
       // repack: running QPs, in thread order, to threads 0 .. n_run - 1
       const unsigned bal = __ballot_sync(wmask, p >= 0);
@@ -351,6 +385,148 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
       if ((int)threadIdx.x < n_run) park_load(threadIdx.x);
       warps = (n_run + 31) / 32;
     }
+  }
+  if (n_run == 0) return;
+  // wide form (see above): group gi (QPW per wide warp) takes record gi,
+  // its lane ci the rows of contact ci and a dense copy of rows 3ci .. 3ci+2
+  // of the grasp's alpha K^-1 (in the parking area, after the records)
+  constexpr int WPC = L::WPC, NVP = L::NVP;
+  const int ci = wl % M, gb = (wl / M) * M;  // contact; first lane of the group in the warp
+  const bool in_group = wl < L::QPW * M;     // lanes past the last whole group stay idle
+  const int gi = warp * L::QPW + (in_group ? wl / M : 0);
+  float wy[3] = {0.f, 0.f, 0.f}, ww[WPC], wmq[3] = {0.f, 0.f, 0.f}, wsum = 0.f;
+#pragma unroll
+  for (int k = 0; k < WPC; ++k) ww[k] = 0.f;
+  const float* Kd = park;  // any valid address for an idle lane
+  p = -1;
+  const bool wide_warp = warp < wide_warps;
+  if (wide_warp && in_group && gi < n_run) {
+    const float* rec = park + gi * L::PW;
+    it = reinterpret_cast<const int*>(rec)[L::pI];
+    p = reinterpret_cast<const int*>(rec)[L::pI + 1];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      wy[r] = rec[3 * ci + r];
+      wmq[r] = rec[L::pM + 3 * ci + r];
+    }
+#pragma unroll
+    for (int k = 0; k < WPC; ++k) ww[k] = rec[L::pW + WPC * ci + k];
+    wsum = rec[L::pW + NC - 1];
+    float* kd = park + wide_warps * L::QPW * L::PW + gi * (NV * NVP) + 3 * ci * NVP;
+    const float* kg = kin(p / S);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int j = 0; j < NVP; ++j) {
+        const int a = min(3 * ci + r, j), b = max(3 * ci + r, j);
+        kd[r * NVP + j] = j < NV ? kg[Admm<M>::tri(a, b)] : 0.f;
+      }
+    Kd = kd;
+  }
+#pragma unroll 1
+  for (;;) {
+    bool run = false;
+    if (wide_warp) {
+        const bool mine = p >= 0;
+        const int g = mine ? p / S : 0;
+        const float rho = per(g)[L::oRho];
+        // running QPs advance in lockstep rounds, so they share `it`
+        const int chunk = __reduce_max_sync(0xffffffffu, mine ? min(check, cfg.iters - it) : 0);
+        const float al = cfg.alpha, bl = 1.0f - cfg.alpha;
+#pragma unroll 1
+        for (int k = 0; k < chunk; ++k) {
+          const float vsum = fmaf(2.f, fmaxf(wsum, cfg.gamma), -wsum);
+          float rhs3[3], pc3[3];
+          if (CONE == CONE_SOC) soc_contact_rhs(ww, vsum, wy, wmq, cfg, rho, rhs3, pc3);
+          else pyr_contact_rhs(ww, vsum, wy, wmq, cfg, rho, rhs3);
+          float ra[NV];
+#pragma unroll
+          for (int j = 0; j < NV; ++j) ra[j] = __shfl_sync(0xffffffffu, rhs3[j % 3], gb + j / 3);
+          float yt3[3];
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            const float4* row = reinterpret_cast<const float4*>(Kd + r * NVP);
+            float acc = 0.f;
+#pragma unroll
+            for (int j4 = 0; j4 < NVP / 4; ++j4) {
+              const float4 kv = row[j4];
+              if (4 * j4 + 0 < NV) acc = fmaf(kv.x, ra[4 * j4 + 0], acc);
+              if (4 * j4 + 1 < NV) acc = fmaf(kv.y, ra[4 * j4 + 1], acc);
+              if (4 * j4 + 2 < NV) acc = fmaf(kv.z, ra[4 * j4 + 2], acc);
+              if (4 * j4 + 3 < NV) acc = fmaf(kv.w, ra[4 * j4 + 3], acc);
+            }
+            yt3[r] = acc;
+          }
+          float sumn = 0.f;
+#pragma unroll
+          for (int i = 0; i < M; ++i) sumn += __shfl_sync(0xffffffffu, yt3[0], gb + i);
+          if (CONE == CONE_SOC) soc_contact_update(ww, pc3, yt3[0], yt3[1], yt3[2], cfg);
+          else pyr_contact_update(ww, yt3[0], yt3[1], yt3[2], cfg);
+          wsum = fmaf(-al, fmaxf(wsum, cfg.gamma), wsum + sumn);
+#pragma unroll
+          for (int r = 0; r < 3; ++r) wy[r] = fmaf(bl, wy[r], yt3[r]);
+        }
+        it += chunk;
+        // residuals, spread over the group: every lane gathers y and forms
+        // G y, then its contact's primal rows and dual components; the group
+        // takes the maxima (the one-lane function's values, bitwise)
+        float ya[NV];
+#pragma unroll
+        for (int j = 0; j < NV; ++j) ya[j] = __shfl_sync(0xffffffffu, wy[j % 3], gb + j / 3);
+        const float* Gg = per(g) + L::oG;
+        float sumn = 0.f, rp = 0.f, rd = 0.f, unused = 0.f;
+#pragma unroll
+        for (int i = 0; i < M; ++i) sumn += ya[3 * i];
+        float at[3];
+        const float psum = fmaxf(wsum, cfg.gamma), dsum = wsum - psum;
+        if (CONE == CONE_SOC) {
+          float dl[4];
+          soc_contact_primal<false>(ww, wy[0], wy[1], wy[2], cfg, rp, unused, dl);
+          at[0] = fmaf(cfg.mu, dl[1], dl[0]) + dsum;
+          at[1] = dl[2];
+          at[2] = dl[3];
+        } else {
+          pyr_contact_primal<false>(ww, wy[0], wy[1], wy[2], cfg, rp, unused);
+          pyr_contact_atd(ww, dsum, cfg, at);
+        }
+        rp = fmaxf(rp, fabsf(sumn - psum));
+        float gy[6];
+        g_times<NV>(Gg, ya, gy);
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+          dual_component<NV, false>(Gg, 3 * ci + q, gy, wy[q], wmq[q], at[q], cfg, rho, rd, unused);
+        float rpg = 0.f, rdg = 0.f;
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          rpg = fmaxf(rpg, __shfl_sync(0xffffffffu, rp, gb + i));
+          rdg = fmaxf(rdg, __shfl_sync(0xffffffffu, rd, gb + i));
+        }
+        const bool conv = rpg <= cfg.eps && rdg <= cfg.eps;
+        const bool done = mine && (conv || it >= cfg.iters);
+        if (__any_sync(0xffffffffu, done)) {
+          // the finished groups' state into their records; their lane 0 writes the results
+          float* rec = park + gi * L::PW;
+          if (done) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) rec[3 * ci + r] = wy[r];
+#pragma unroll
+            for (int k = 0; k < WPC; ++k) rec[L::pW + WPC * ci + k] = ww[k];
+            if (ci == 0) rec[L::pW + NC - 1] = wsum;
+          }
+          __syncwarp();
+          if (done && ci == 0) {
+#pragma unroll
+            for (int a = 0; a < NV; ++a) y[a] = rec[a];
+#pragma unroll
+            for (int r = 0; r < NC; ++r) w[r] = rec[L::pW + r];
+            finish(p, rpg, rdg, conv);
+          }
+          __syncwarp();
+        }
+        run = mine && !done && ci == 0;
+        if (done) p = -1;
+      }
+    if (__syncthreads_count(run) == 0) break;
   }
 }
 

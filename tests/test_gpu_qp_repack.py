@@ -13,13 +13,16 @@ import paper_2412_16490_gb300 as bx
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("m,cone", [(5, 0), (3, 0), (4, 1), (5, 1)])
 @pytest.mark.parametrize("s", [12, 7])
 @pytest.mark.parametrize("adaptive", [0, 1])
-def test_qp_results_do_not_depend_on_the_batch(s, adaptive):
+def test_qp_results_do_not_depend_on_the_batch(m, cone, s, adaptive):
+    """Also covers the wide form (the last QPs of a CTA, m lanes each): which
+    QPs reach it, and when, depends on the batch."""
     T = cuda(I.wrench_set(12)[:s].copy())
-    p, n = I.random_contacts(50, 5, seed=95)
+    p, n = I.random_contacts(50, m, seed=95 + m)
     G = cuda(O.grasp_matrix(p, n).astype(np.float32))
-    prm = bx.qp_params(eps_abs=1e-5, max_iter=3000, check_every=10, adaptive_rho=adaptive)
+    prm = bx.qp_params(eps_abs=1e-5, max_iter=3000, check_every=10, adaptive_rho=adaptive, cone=cone)
     full = bx.bodex_qp_solve_batch(G, T, prm)
     sub = bx.bodex_qp_solve_batch(G[3:41].contiguous(), T, prm)  # every grasp in another CTA position
     for k in ("y", "z", "lam", "Q", "iters", "status", "res"):

@@ -37,7 +37,7 @@ SM_COUNT, FP32_LANES = 152, 128
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused_kernel<5, step> launch on this
 # workload (profiles/fused_step_paper_4096.md; a 5-step launch of the same kernel -- the state
 # is read once per launch and the grid stays in L2, so the bytes do not grow with the steps)
-TRAFFIC_BYTES = 14_551_552 + 1_280
+TRAFFIC_BYTES = 14_551_040 + 2_304
 TRAFFIC_SOURCE = "ncu capture in profiles/fused_step_paper_4096.md (5-step launch; per-launch bytes)"
 
 

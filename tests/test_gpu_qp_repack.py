@@ -39,3 +39,30 @@ def test_fixed_iteration_batch_runs_every_qp_to_the_cap():
     assert (host(out["iters"]) == 37).all()
     assert (host(out["status"]) == 0).all()
     assert np.isfinite(host(out["Q"])).all() and (host(out["res"]) >= 0).all()
+
+
+@pytest.mark.parametrize("B,s", [(1, 12), (1, 1), (200, 1), (13, 16), (0, 12)])
+def test_qp_repacking_edge_shapes(B, s):
+    """One grasp (a single partial warp: no wide form), one wrench per grasp
+    (88 grasps per CTA, a partial last warp), the widest wrench set, and an
+    empty batch: results match the same QPs solved one grasp at a time."""
+    if s <= 12:
+        T = I.wrench_set(12)[:s].copy()
+    else:  # the 12 axes and unit force diagonals
+        diag = np.zeros((s - 12, 6), np.float32)
+        for k in range(s - 12):
+            diag[k, k % 3], diag[k, (k + 1) % 3] = 0.6, 0.8
+        T = np.concatenate([I.wrench_set(12), diag])
+    T = cuda(T)
+    p, n = I.random_contacts(max(B, 1), 5, seed=97)
+    G = cuda(O.grasp_matrix(p, n).astype(np.float32))[:B].contiguous()
+    prm = bx.qp_params(eps_abs=1e-5, max_iter=3000, check_every=10)
+    full = bx.bodex_qp_solve_batch(G, T, prm)
+    assert full["Q"].shape == (B, s)
+    for b in range(0, B, max(1, B // 5)):
+        one = bx.bodex_qp_solve_batch(G[b:b + 1].contiguous(), T, prm)
+        for k in ("y", "z", "lam", "Q", "iters", "status"):
+            assert torch.equal(full[k][b:b + 1], one[k]), (b, k)
+    if B:
+        conv = (host(full["status"]) & bx.ST_NOT_CONVERGED) == 0
+        assert conv.mean() > 0.9

@@ -302,6 +302,15 @@ typedef struct bodex_job {
 } bodex_job;
 int bodex_step_multi(const bodex_job* jobs, int n_jobs, const bodex_step_params* params, void* stream);
 
+/* The CTA tile the fused step kernel uses for m contacts and s wrenches:
+ * `requested` grasps per thread block (0: the default, 96 / s), capped by
+ * 96 lanes and by the shared memory of one block.  A job of B grasps then
+ * occupies ceil(B / tile) thread blocks, which is how a scheduler fills one
+ * wave of the GPU (4 blocks per SM).  Host-only: touches no device.
+ * Errors: BODEX_ERR_INVALID (m outside 3..5, s outside 1..16,
+ * requested < 0, null output). */
+int bodex_step_tile(int m, int s, int requested, int* grasps_per_cta);
+
 /* Backward pass of the energy for forces y from an earlier solve (the
  * hand-written adjoint behind the autograd binding): recomputes FK, the SDF
  * query and G at x, forms r_j = beta t_j - G y_j, Q_j = |r_j|^2 and E, and

@@ -21,7 +21,7 @@ __all__ = [
     "bodex_hand_create", "bodex_object_create", "bodex_state_create",
     "bodex_fk_contacts", "bodex_qp_solve_batch", "bodex_energy_grad", "bodex_energy_adjoint", "bodex_step", "bodex_step_multi", "bodex_refine",
     "synthesize",
-    "bodex_sync", "bodex_version", "BodexError",
+    "bodex_sync", "bodex_version", "bodex_step_tile", "BodexError",
 ]
 
 
@@ -353,3 +353,11 @@ def bodex_sync(stream=None):
 
 def bodex_version() -> str:
     return load().bodex_version().decode()
+
+
+def bodex_step_tile(m: int, s: int, requested: int = 0) -> int:
+    """Grasps per thread block the fused step kernel uses for m contacts and
+    s wrenches (`requested` = grasps_per_cta, 0 for the default).  Host-only."""
+    out = C.c_int(0)
+    _b.check(load().bodex_step_tile(int(m), int(s), int(requested), C.byref(out)))
+    return out.value

@@ -33,7 +33,7 @@ EXPORTS = (
     "bodex_hand_create", "bodex_hand_destroy", "bodex_object_create", "bodex_object_destroy",
     "bodex_object_gravity_centre", "bodex_fk_contacts", "bodex_qp_solve_batch", "bodex_state_create",
     "bodex_state_destroy", "bodex_state_set_pose", "bodex_state_get_pose", "bodex_state_get_adam",
-    "bodex_state_get_residual", "bodex_step_multi",
+    "bodex_state_get_residual", "bodex_step_multi", "bodex_step_tile",
     "bodex_energy_grad", "bodex_energy_adjoint", "bodex_step", "bodex_refine", "bodex_contact_metrics", "bodex_step_noalloc", "bodex_sync", "bodex_last_error", "bodex_version",
 )
 
@@ -122,6 +122,7 @@ def load(build_if_missing: bool = True):
         "bodex_state_get_adam": [v, v, v, C.POINTER(C.c_int), v],
         "bodex_state_get_residual": [v, v, v],
         "bodex_step_multi": [C.POINTER(bodex_job), C.c_int, C.POINTER(bodex_step_params), v],
+        "bodex_step_tile": [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int)],
         "bodex_energy_grad": [v, v, v, C.c_int, v, C.c_int, C.POINTER(bodex_step_params), v, v, v, v, v, v, v],
         "bodex_energy_adjoint": [v, v, v, C.c_int, v, C.c_int, C.POINTER(bodex_step_params), v, v, v, v, v],
         "bodex_step": [v, v, v, v, C.c_int, C.c_int, C.POINTER(bodex_step_params), v, v, v],

@@ -529,6 +529,18 @@ extern "C" {
 const char* bodex_last_error(void) { return g_err.c_str(); }
 const char* bodex_version(void) { return "bodex-gb300 0.1 (sm_103a)"; }
 
+int bodex_step_tile(int m, int s, int requested, int* grasps_per_cta) {
+  if (!grasps_per_cta || s < 1 || s > SMAX || requested < 0)
+    return fail(BODEX_ERR_INVALID, "bodex_step_tile: s outside 1..16, requested < 0 or null output");
+  switch (m) {
+    case 3: *grasps_per_cta = pick_gpb<3>(s, requested); break;
+    case 4: *grasps_per_cta = pick_gpb<4>(s, requested); break;
+    case 5: *grasps_per_cta = pick_gpb<5>(s, requested); break;
+    default: return fail(BODEX_ERR_INVALID, "bodex_step_tile: m must be 3, 4 or 5");
+  }
+  return BODEX_OK;
+}
+
 int bodex_sync(void* stream) {
   BODEX_CUDA(cudaStreamSynchronize(as_stream(stream)));
   return BODEX_OK;

@@ -23,11 +23,10 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Hand, Object, State, bodex_step, bodex_step_multi, step_params
+from . import Hand, Object, State, bodex_step, bodex_step_multi, bodex_step_tile, step_params
 from ._binding import BODEX_MAX_JOBS
 
-CTA_LANES = 96    # threads per thread block of the fused step kernel
-CTAS_PER_SM = 4   # its resident blocks per SM (register bound)
+CTAS_PER_SM = 4   # resident thread blocks of the fused step kernel per SM (register bound)
 
 
 @dataclass
@@ -232,7 +231,7 @@ class Server(_Base):
         return bool(self.active or self._waiting or self.finishing)
 
     def _job_ctas(self, spec) -> int:
-        gpb = self.params.grasps_per_cta or max(1, CTA_LANES // spec.T.shape[0])
+        gpb = bodex_step_tile(spec.hand.n_contacts, spec.T.shape[0], self.params.grasps_per_cta)
         return -(-spec.x0.shape[0] // gpb)
 
     def _new_state(self, spec, hand) -> State:

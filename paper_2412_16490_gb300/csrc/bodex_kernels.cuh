@@ -119,20 +119,22 @@ __device__ inline void setup_kinv(bool active, int lane, int S, const float* Gs,
 // ============================================================================ kernel: batched QP
 // One QP per thread, the grasps' K^-1 shared by their QPs.  QPs converge
 // after very different iteration counts (at 1e-5 on the paper geometry the
-// median is 400, the slowest of a warp's 32 about 1700), and a warp runs
+// median is 400, the slowest of a warp's 32 about 3100), and a warp runs
 // until its last QP stops.  So at every residual check the QPs still running
 // are repacked, through shared memory, into the lowest warps of the CTA: a
 // warp whose QPs all stopped waits at the barrier and issues nothing while
 // the others iterate.  A QP carries its iterate, -q, its iteration count and
 // its slot (grasp, wrench); K^-1, G and rho stay with the grasp.
-// The last QPs of a CTA (at most 32 / m per full warp) run in a wide form:
-// one QP per m lanes of a warp, lane i holding contact i's rows, the rhs exchanged by
-// warp shuffles and each lane forming three rows of alpha K^-1 rhs from a
-// dense copy of the grasp's K^-1.  An iteration then costs a few hundred
-// cycles of dependent latency instead of about a thousand, which is what
-// the slowest QPs of a batch run at.  Every multiply-add is the one-lane
-// form's, in the same order (row r of the product sums j = 0 .. nv-1 in
-// both), so the iterates agree bitwise.  Not used with adaptive rho.
+// The last QPs of a CTA (at most 32 / m) run in a wide form on warp 0: one
+// QP per m lanes, lane i holding contact i's rows, the rhs exchanged by warp
+// shuffles and each lane forming three rows of alpha K^-1 rhs from a dense
+// copy of the grasp's K^-1; the residual check is spread over the lanes
+// too.  Alone on its SM, a QP's iteration is bound by its chain of dependent
+// instructions, which the wide form shortens: the slowest QPs of a batch
+// finish sooner (the paper batch: 2.64 ms instead of 3.26 ms).  Every
+// multiply-add is the one-lane form's, in the same order (row r of the
+// product sums j = 0 .. nv-1 in both), so the iterates agree bitwise.  Not
+// used with adaptive rho.
 //
 // Shared memory: alpha K^-1 per grasp (stride as in the fused kernel), the
 // per-grasp block (G, Woodbury scratch, votes, rho), the parking area (one
@@ -275,11 +277,11 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
   const int nw = min(32, (int)blockDim.x - 32 * warp);
   const unsigned wmask = nw == 32 ? 0xffffffffu : (1u << nw) - 1u;  // this warp's threads
   int warps = (blockDim.x + 31) / 32;                                  // warps that hold running QPs
-  // warps that take wide groups (full warps that the parking area has room
-  // for), at most one: on the 49k-QP paper batch, groups in every warp of the
-  // CTA (up to 18 QPs at m = 5) took 3.05 ms against 2.68 ms with warp 0
-  // alone, the SMs turning issue-bound again
-  const int wide_warps = min(min(1, (int)blockDim.x / 32), GPB * S * L::PW / (L::QPW * L::WIDE_PER_QP));
+  // warps that take wide groups: warp 0 when it is full and the parking area
+  // has room.  (Groups in every full warp, up to 18 QPs at m = 5, took
+  // 3.05 ms on the paper batch against 2.68 ms for warp 0 alone: the SMs
+  // turn issue-bound again.)
+  const int wide_warps = (blockDim.x >= 32 && GPB * S * L::PW >= L::QPW * L::WIDE_PER_QP) ? 1 : 0;
   const bool wide_ok = !adaptive && cfg.eps > 0.f && wide_warps > 0;
   int n_run;
 #pragma unroll 1
@@ -427,105 +429,105 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
   for (;;) {
     bool run = false;
     if (wide_warp) {
-        const bool mine = p >= 0;
-        const int g = mine ? p / S : 0;
-        const float rho = per(g)[L::oRho];
-        // running QPs advance in lockstep rounds, so they share `it`
-        const int chunk = __reduce_max_sync(0xffffffffu, mine ? min(check, cfg.iters - it) : 0);
-        const float al = cfg.alpha, bl = 1.0f - cfg.alpha;
+      const bool mine = p >= 0;
+      const int g = mine ? p / S : 0;
+      const float rho = per(g)[L::oRho];
+      // running QPs advance in lockstep rounds, so they share `it`
+      const int chunk = __reduce_max_sync(0xffffffffu, mine ? min(check, cfg.iters - it) : 0);
+      const float al = cfg.alpha, bl = 1.0f - cfg.alpha;
 #pragma unroll 1
-        for (int k = 0; k < chunk; ++k) {
-          const float vsum = fmaf(2.f, fmaxf(wsum, cfg.gamma), -wsum);
-          float rhs3[3], pc3[3];
-          if (CONE == CONE_SOC) soc_contact_rhs(ww, vsum, wy, wmq, cfg, rho, rhs3, pc3);
-          else pyr_contact_rhs(ww, vsum, wy, wmq, cfg, rho, rhs3);
-          float ra[NV];
+      for (int k = 0; k < chunk; ++k) {
+        const float vsum = fmaf(2.f, fmaxf(wsum, cfg.gamma), -wsum);
+        float rhs3[3], pc3[3];
+        if (CONE == CONE_SOC) soc_contact_rhs(ww, vsum, wy, wmq, cfg, rho, rhs3, pc3);
+        else pyr_contact_rhs(ww, vsum, wy, wmq, cfg, rho, rhs3);
+        float ra[NV];
 #pragma unroll
-          for (int j = 0; j < NV; ++j) ra[j] = __shfl_sync(0xffffffffu, rhs3[j % 3], gb + j / 3);
-          float yt3[3];
+        for (int j = 0; j < NV; ++j) ra[j] = __shfl_sync(0xffffffffu, rhs3[j % 3], gb + j / 3);
+        float yt3[3];
 #pragma unroll
-          for (int r = 0; r < 3; ++r) {
-            const float4* row = reinterpret_cast<const float4*>(Kd + r * NVP);
-            float acc = 0.f;
+        for (int r = 0; r < 3; ++r) {
+          const float4* row = reinterpret_cast<const float4*>(Kd + r * NVP);
+          float acc = 0.f;
 #pragma unroll
-            for (int j4 = 0; j4 < NVP / 4; ++j4) {
-              const float4 kv = row[j4];
-              if (4 * j4 + 0 < NV) acc = fmaf(kv.x, ra[4 * j4 + 0], acc);
-              if (4 * j4 + 1 < NV) acc = fmaf(kv.y, ra[4 * j4 + 1], acc);
-              if (4 * j4 + 2 < NV) acc = fmaf(kv.z, ra[4 * j4 + 2], acc);
-              if (4 * j4 + 3 < NV) acc = fmaf(kv.w, ra[4 * j4 + 3], acc);
-            }
-            yt3[r] = acc;
+          for (int j4 = 0; j4 < NVP / 4; ++j4) {
+            const float4 kv = row[j4];
+            if (4 * j4 + 0 < NV) acc = fmaf(kv.x, ra[4 * j4 + 0], acc);
+            if (4 * j4 + 1 < NV) acc = fmaf(kv.y, ra[4 * j4 + 1], acc);
+            if (4 * j4 + 2 < NV) acc = fmaf(kv.z, ra[4 * j4 + 2], acc);
+            if (4 * j4 + 3 < NV) acc = fmaf(kv.w, ra[4 * j4 + 3], acc);
           }
-          float sumn = 0.f;
-#pragma unroll
-          for (int i = 0; i < M; ++i) sumn += __shfl_sync(0xffffffffu, yt3[0], gb + i);
-          if (CONE == CONE_SOC) soc_contact_update(ww, pc3, yt3[0], yt3[1], yt3[2], cfg);
-          else pyr_contact_update(ww, yt3[0], yt3[1], yt3[2], cfg);
-          wsum = fmaf(-al, fmaxf(wsum, cfg.gamma), wsum + sumn);
-#pragma unroll
-          for (int r = 0; r < 3; ++r) wy[r] = fmaf(bl, wy[r], yt3[r]);
+          yt3[r] = acc;
         }
-        it += chunk;
-        // residuals, spread over the group: every lane gathers y and forms
-        // G y, then its contact's primal rows and dual components; the group
-        // takes the maxima (the one-lane function's values, bitwise)
-        float ya[NV];
+        float sumn = 0.f;
 #pragma unroll
-        for (int j = 0; j < NV; ++j) ya[j] = __shfl_sync(0xffffffffu, wy[j % 3], gb + j / 3);
-        const float* Gg = per(g) + L::oG;
-        float sumn = 0.f, rp = 0.f, rd = 0.f, unused = 0.f;
+        for (int i = 0; i < M; ++i) sumn += __shfl_sync(0xffffffffu, yt3[0], gb + i);
+        if (CONE == CONE_SOC) soc_contact_update(ww, pc3, yt3[0], yt3[1], yt3[2], cfg);
+        else pyr_contact_update(ww, yt3[0], yt3[1], yt3[2], cfg);
+        wsum = fmaf(-al, fmaxf(wsum, cfg.gamma), wsum + sumn);
 #pragma unroll
-        for (int i = 0; i < M; ++i) sumn += ya[3 * i];
-        float at[3];
-        const float psum = fmaxf(wsum, cfg.gamma), dsum = wsum - psum;
-        if (CONE == CONE_SOC) {
-          float dl[4];
-          soc_contact_primal<false>(ww, wy[0], wy[1], wy[2], cfg, rp, unused, dl);
-          at[0] = fmaf(cfg.mu, dl[1], dl[0]) + dsum;
-          at[1] = dl[2];
-          at[2] = dl[3];
-        } else {
-          pyr_contact_primal<false>(ww, wy[0], wy[1], wy[2], cfg, rp, unused);
-          pyr_contact_atd(ww, dsum, cfg, at);
-        }
-        rp = fmaxf(rp, fabsf(sumn - psum));
-        float gy[6];
-        g_times<NV>(Gg, ya, gy);
-#pragma unroll
-        for (int q = 0; q < 3; ++q)
-          dual_component<NV, false>(Gg, 3 * ci + q, gy, wy[q], wmq[q], at[q], cfg, rho, rd, unused);
-        float rpg = 0.f, rdg = 0.f;
-#pragma unroll
-        for (int i = 0; i < M; ++i) {
-          rpg = fmaxf(rpg, __shfl_sync(0xffffffffu, rp, gb + i));
-          rdg = fmaxf(rdg, __shfl_sync(0xffffffffu, rd, gb + i));
-        }
-        const bool conv = rpg <= cfg.eps && rdg <= cfg.eps;
-        const bool done = mine && (conv || it >= cfg.iters);
-        if (__any_sync(0xffffffffu, done)) {
-          // the finished groups' state into their records; their lane 0 writes the results
-          float* rec = park + gi * L::PW;
-          if (done) {
-#pragma unroll
-            for (int r = 0; r < 3; ++r) rec[3 * ci + r] = wy[r];
-#pragma unroll
-            for (int k = 0; k < WPC; ++k) rec[L::pW + WPC * ci + k] = ww[k];
-            if (ci == 0) rec[L::pW + NC - 1] = wsum;
-          }
-          __syncwarp();
-          if (done && ci == 0) {
-#pragma unroll
-            for (int a = 0; a < NV; ++a) y[a] = rec[a];
-#pragma unroll
-            for (int r = 0; r < NC; ++r) w[r] = rec[L::pW + r];
-            finish(p, rpg, rdg, conv);
-          }
-          __syncwarp();
-        }
-        run = mine && !done && ci == 0;
-        if (done) p = -1;
+        for (int r = 0; r < 3; ++r) wy[r] = fmaf(bl, wy[r], yt3[r]);
       }
+      it += chunk;
+      // residuals, spread over the group: every lane gathers y and forms
+      // G y, then its contact's primal rows and dual components; the group
+      // takes the maxima (the one-lane function's values, bitwise)
+      float ya[NV];
+#pragma unroll
+      for (int j = 0; j < NV; ++j) ya[j] = __shfl_sync(0xffffffffu, wy[j % 3], gb + j / 3);
+      const float* Gg = per(g) + L::oG;
+      float sumn = 0.f, rp = 0.f, rd = 0.f, unused = 0.f;
+#pragma unroll
+      for (int i = 0; i < M; ++i) sumn += ya[3 * i];
+      float at[3];
+      const float psum = fmaxf(wsum, cfg.gamma), dsum = wsum - psum;
+      if (CONE == CONE_SOC) {
+        float dl[4];
+        soc_contact_primal<false>(ww, wy[0], wy[1], wy[2], cfg, rp, unused, dl);
+        at[0] = fmaf(cfg.mu, dl[1], dl[0]) + dsum;
+        at[1] = dl[2];
+        at[2] = dl[3];
+      } else {
+        pyr_contact_primal<false>(ww, wy[0], wy[1], wy[2], cfg, rp, unused);
+        pyr_contact_atd(ww, dsum, cfg, at);
+      }
+      rp = fmaxf(rp, fabsf(sumn - psum));
+      float gy[6];
+      g_times<NV>(Gg, ya, gy);
+#pragma unroll
+      for (int q = 0; q < 3; ++q)
+        dual_component<NV, false>(Gg, 3 * ci + q, gy, wy[q], wmq[q], at[q], cfg, rho, rd, unused);
+      float rpg = 0.f, rdg = 0.f;
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        rpg = fmaxf(rpg, __shfl_sync(0xffffffffu, rp, gb + i));
+        rdg = fmaxf(rdg, __shfl_sync(0xffffffffu, rd, gb + i));
+      }
+      const bool conv = rpg <= cfg.eps && rdg <= cfg.eps;
+      const bool done = mine && (conv || it >= cfg.iters);
+      if (__any_sync(0xffffffffu, done)) {
+        // the finished groups' state into their records; their lane 0 writes the results
+        float* rec = park + gi * L::PW;
+        if (done) {
+#pragma unroll
+          for (int r = 0; r < 3; ++r) rec[3 * ci + r] = wy[r];
+#pragma unroll
+          for (int k = 0; k < WPC; ++k) rec[L::pW + WPC * ci + k] = ww[k];
+          if (ci == 0) rec[L::pW + NC - 1] = wsum;
+        }
+        __syncwarp();
+        if (done && ci == 0) {
+#pragma unroll
+          for (int a = 0; a < NV; ++a) y[a] = rec[a];
+#pragma unroll
+          for (int r = 0; r < NC; ++r) w[r] = rec[L::pW + r];
+          finish(p, rpg, rdg, conv);
+        }
+        __syncwarp();
+      }
+      run = mine && !done && ci == 0;
+      if (done) p = -1;
+    }
     if (__syncthreads_count(run) == 0) break;
   }
 }

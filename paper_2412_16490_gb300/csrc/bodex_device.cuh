@@ -1014,29 +1014,40 @@ __device__ inline int admm_solve(float* y, float* w, const float* mq, const floa
 
 // Re-expresses the iterate for a new penalty rho' (ratio = rho / rho'),
 // keeping z = Pi(w) and lam = rho (w - Pi(w)): w <- Pi(w) + ratio (w - Pi(w)).
-template <int M, int CONE>
-__device__ inline void rescale_w(float* w, float ratio, const AdmmCfg& c) {
+// Per contact (its rows: f_n and the facets, or f_n and the cone triple) and
+// for the sum row; rescale_w and the wide form of the batched QP kernel
+// share these.
+template <int CONE>
+__device__ __forceinline__ void rescale_contact(float* wi, float ratio) {
   if (CONE == CONE_SOC) {
-#pragma unroll
-    for (int i = 0; i < M; ++i) {
-      float* wi = w + 4 * i;
-      const float p0 = __saturatef(wi[0]);
-      wi[0] = fmaf(ratio, wi[0] - p0, p0);
-      float ps, p1, p2;
-      proj_soc(wi[1], wi[2], wi[3], ps, p1, p2);
-      wi[1] = fmaf(ratio, wi[1] - ps, ps);
-      wi[2] = fmaf(ratio, wi[2] - p1, p1);
-      wi[3] = fmaf(ratio, wi[3] - p2, p2);
-    }
-    const float ps = fmaxf(w[4 * M], c.gamma);
-    w[4 * M] = fmaf(ratio, w[4 * M] - ps, ps);
+    const float p0 = __saturatef(wi[0]);
+    wi[0] = fmaf(ratio, wi[0] - p0, p0);
+    float ps, p1, p2;
+    proj_soc(wi[1], wi[2], wi[3], ps, p1, p2);
+    wi[1] = fmaf(ratio, wi[1] - ps, ps);
+    wi[2] = fmaf(ratio, wi[2] - p1, p1);
+    wi[3] = fmaf(ratio, wi[3] - p2, p2);
   } else {
+    const float p0 = fminf(fmaxf(wi[0], 0.f), 1.f);
+    wi[0] = fmaf(ratio, wi[0] - p0, p0);
 #pragma unroll
-    for (int r = 0; r < 9 * M + 1; ++r) {
-      const float p = proj_row<M>(w[r], r, c.gamma);
-      w[r] = fmaf(ratio, w[r] - p, p);
+    for (int k = 1; k < 9; ++k) {
+      const float p = fminf(wi[k], 0.f);
+      wi[k] = fmaf(ratio, wi[k] - p, p);
     }
   }
+}
+__device__ __forceinline__ float rescale_sum_row(float wsum, float ratio, float gamma) {
+  const float p = fmaxf(wsum, gamma);
+  return fmaf(ratio, wsum - p, p);
+}
+
+template <int M, int CONE>
+__device__ inline void rescale_w(float* w, float ratio, const AdmmCfg& c) {
+  constexpr int RPC = CONE == CONE_SOC ? 4 : 9;  // rows per contact
+#pragma unroll
+  for (int i = 0; i < M; ++i) rescale_contact<CONE>(w + RPC * i, ratio);
+  w[RPC * M] = rescale_sum_row(w[RPC * M], ratio, c.gamma);
 }
 
 // One QP's proposal for log(rho' / rho) in residual balancing (OSQP,

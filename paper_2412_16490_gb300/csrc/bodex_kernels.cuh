@@ -133,8 +133,7 @@ __device__ inline void setup_kinv(bool active, int lane, int S, const float* Gs,
 // instructions, which the wide form shortens: the slowest QPs of a batch
 // finish sooner (the paper batch: 2.64 ms instead of 3.26 ms).  Every
 // multiply-add is the one-lane form's, in the same order (row r of the
-// product sums j = 0 .. nv-1 in both), so the iterates agree bitwise.  Not
-// used with adaptive rho.
+// product sums j = 0 .. nv-1 in both), so the iterates agree bitwise.
 //
 // Shared memory: alpha K^-1 per grasp (stride as in the fused kernel), the
 // per-grasp block (G, Woodbury scratch, votes, rho), the parking area (one
@@ -273,6 +272,37 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
     it = reinterpret_cast<const int*>(rec)[L::pI];
     p = reinterpret_cast<const int*>(rec)[L::pI + 1];
   };
+  // adaptive rho, one decision per grasp (lane 0 of its setup role): rho
+  // moves by the geometric mean of its running QPs' proposals when that is
+  // more than 5x (clamped to [1e-6, 1e6]); returns whether it moved
+  auto decide = [&]() -> bool {
+    if (!(role && lane == 0)) return false;
+    float* pg = per(gl);
+    float sh = 0.f;
+    int cnt = 0;
+    for (int j = 0; j < S; ++j) {
+      const float v = pg[L::oVote + j];
+      sh += v;
+      cnt += v != 0.f;
+    }
+    const float cur = pg[L::oRho];
+    float nxt = cur;
+    if (cnt > 0 && fabsf(sh / cnt) > 1.6094379f)  // log 5
+      nxt = fminf(fmaxf(cur * __expf(sh / cnt), 1e-6f), 1e6f);
+    pg[L::oRho + 1] = cur;
+    pg[L::oRho] = nxt;
+    return nxt != cur;
+  };
+  // K^-1 of the grasps whose rho moved (every thread; barriers inside)
+  auto rebuild = [&]() {
+    AdmmCfg cl = cfg;
+    bool upd = false;
+    if (role) {
+      cl.rho = per(gl)[L::oRho];
+      upd = cl.rho != per(gl)[L::oRho + 1];
+    }
+    setup_kinv<M>(upd, lane, S, per(gl) + L::oG, per(gl) + L::oK, kin(gl), cl);
+  };
   const int warp = threadIdx.x / 32, wl = threadIdx.x % 32;
   const int nw = min(32, (int)blockDim.x - 32 * warp);
   const unsigned wmask = nw == 32 ? 0xffffffffu : (1u << nw) - 1u;  // this warp's threads
@@ -282,7 +312,7 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
   // 3.05 ms on the paper batch against 2.68 ms for warp 0 alone: the SMs
   // turn issue-bound again.)
   const int wide_warps = (blockDim.x >= 32 && GPB * S * L::PW >= L::QPW * L::WIDE_PER_QP) ? 1 : 0;
-  const bool wide_ok = !adaptive && cfg.eps > 0.f && wide_warps > 0;
+  const bool wide_ok = cfg.eps > 0.f && wide_warps > 0;
   int n_run;
 #pragma unroll 1
   for (;;) {
@@ -322,40 +352,14 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
     n_run = __syncthreads_count(run);
     if (n_run == 0) break;
     if (adaptive) {
-      // one decision per grasp: rho moves by the geometric mean of its running
-      // QPs' proposals when that is more than 5x (clamped to [1e-6, 1e6])
-      bool moved = false;
-      if (role && lane == 0) {
-        float* pg = per(gl);
-        float sh = 0.f;
-        int cnt = 0;
-        for (int j = 0; j < S; ++j) {
-          const float v = pg[L::oVote + j];
-          sh += v;
-          cnt += v != 0.f;
-        }
-        const float cur = pg[L::oRho];
-        float nxt = cur;
-        if (cnt > 0 && fabsf(sh / cnt) > 1.6094379f)  // log 5
-          nxt = fminf(fmaxf(cur * __expf(sh / cnt), 1e-6f), 1e6f);
-        pg[L::oRho + 1] = cur;
-        pg[L::oRho] = nxt;
-        moved = nxt != cur;
-      }
-      if (!__syncthreads_or(moved)) goto repack;  // no grasp of the CTA changed rho
+      if (!__syncthreads_or(decide())) goto repack;  // no grasp of the CTA changed rho
       const bool mine = p >= 0;
       if (mine) {  // re-express the iterate at the grasp's new rho, then park it (its registers go to the setup)
         const float* pg = per(p / S);
         if (pg[L::oRho] != pg[L::oRho + 1]) rescale_w<M, CONE>(w, pg[L::oRho + 1] / pg[L::oRho], cfg);
         park_store(threadIdx.x);
       }
-      AdmmCfg cl = cfg;
-      bool upd = false;
-      if (role) {
-        cl.rho = per(gl)[L::oRho];
-        upd = cl.rho != per(gl)[L::oRho + 1];
-      }
-      setup_kinv<M>(upd, lane, S, per(gl) + L::oG, per(gl) + L::oK, kin(gl), cl);  // barriers inside
+      rebuild();
       if (mine) park_load(threadIdx.x);
     }
   repack:
@@ -399,7 +403,7 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
   float wy[3] = {0.f, 0.f, 0.f}, ww[WPC], wmq[3] = {0.f, 0.f, 0.f}, wsum = 0.f;
 #pragma unroll
   for (int k = 0; k < WPC; ++k) ww[k] = 0.f;
-  const float* Kd = park;  // any valid address for an idle lane
+  float* Kd = park;  // any valid address for an idle lane
   p = -1;
   const bool wide_warp = warp < wide_warps;
   if (wide_warp && in_group && gi < n_run) {
@@ -414,17 +418,20 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
 #pragma unroll
     for (int k = 0; k < WPC; ++k) ww[k] = rec[L::pW + WPC * ci + k];
     wsum = rec[L::pW + NC - 1];
-    float* kd = park + wide_warps * L::QPW * L::PW + gi * (NV * NVP) + 3 * ci * NVP;
+    Kd = park + wide_warps * L::QPW * L::PW + gi * (NV * NVP) + 3 * ci * NVP;
+  }
+  // rows 3ci .. 3ci+2 of the grasp's alpha K^-1, dense (this lane's own rows)
+  auto copy_rows = [&]() {
     const float* kg = kin(p / S);
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int j = 0; j < NVP; ++j) {
         const int a = min(3 * ci + r, j), b = max(3 * ci + r, j);
-        kd[r * NVP + j] = j < NV ? kg[Admm<M>::tri(a, b)] : 0.f;
+        Kd[r * NVP + j] = j < NV ? kg[Admm<M>::tri(a, b)] : 0.f;
       }
-    Kd = kd;
-  }
+  };
+  if (p >= 0) copy_rows();
 #pragma unroll 1
   for (;;) {
     bool run = false;
@@ -476,32 +483,35 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
 #pragma unroll
       for (int j = 0; j < NV; ++j) ya[j] = __shfl_sync(0xffffffffu, wy[j % 3], gb + j / 3);
       const float* Gg = per(g) + L::oG;
-      float sumn = 0.f, rp = 0.f, rd = 0.f, unused = 0.f;
+      float sumn = 0.f, rp = 0.f, rd = 0.f, np = 0.f, nd = 0.f;
 #pragma unroll
       for (int i = 0; i < M; ++i) sumn += ya[3 * i];
       float at[3];
       const float psum = fmaxf(wsum, cfg.gamma), dsum = wsum - psum;
       if (CONE == CONE_SOC) {
         float dl[4];
-        soc_contact_primal<false>(ww, wy[0], wy[1], wy[2], cfg, rp, unused, dl);
+        soc_contact_primal<true>(ww, wy[0], wy[1], wy[2], cfg, rp, np, dl);
         at[0] = fmaf(cfg.mu, dl[1], dl[0]) + dsum;
         at[1] = dl[2];
         at[2] = dl[3];
       } else {
-        pyr_contact_primal<false>(ww, wy[0], wy[1], wy[2], cfg, rp, unused);
+        pyr_contact_primal<true>(ww, wy[0], wy[1], wy[2], cfg, rp, np);
         pyr_contact_atd(ww, dsum, cfg, at);
       }
       rp = fmaxf(rp, fabsf(sumn - psum));
+      np = fmaxf(np, fmaxf(fabsf(sumn), fabsf(psum)));
       float gy[6];
       g_times<NV>(Gg, ya, gy);
 #pragma unroll
       for (int q = 0; q < 3; ++q)
-        dual_component<NV, false>(Gg, 3 * ci + q, gy, wy[q], wmq[q], at[q], cfg, rho, rd, unused);
-      float rpg = 0.f, rdg = 0.f;
+        dual_component<NV, true>(Gg, 3 * ci + q, gy, wy[q], wmq[q], at[q], cfg, rho, rd, nd);
+      float rpg = 0.f, rdg = 0.f, scale[2] = {0.f, 0.f};  // group maxima
 #pragma unroll
       for (int i = 0; i < M; ++i) {
         rpg = fmaxf(rpg, __shfl_sync(0xffffffffu, rp, gb + i));
         rdg = fmaxf(rdg, __shfl_sync(0xffffffffu, rd, gb + i));
+        scale[0] = fmaxf(scale[0], __shfl_sync(0xffffffffu, np, gb + i));
+        scale[1] = fmaxf(scale[1], __shfl_sync(0xffffffffu, nd, gb + i));
       }
       const bool conv = rpg <= cfg.eps && rdg <= cfg.eps;
       const bool done = mine && (conv || it >= cfg.iters);
@@ -526,9 +536,22 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
         __syncwarp();
       }
       run = mine && !done && ci == 0;
+      if (adaptive && mine && ci == 0) per(g)[L::oVote + p % S] = done ? 0.f : rho_vote(rpg, rdg, scale);
       if (done) p = -1;
     }
     if (__syncthreads_count(run) == 0) break;
+    if (adaptive && __syncthreads_or(decide())) {
+      // the wide lanes re-express their rows at the grasp's new rho; after the
+      // rebuild they refresh their dense rows of K^-1
+      const bool moved = p >= 0 && per(p / S)[L::oRho] != per(p / S)[L::oRho + 1];
+      if (moved) {
+        const float ratio = per(p / S)[L::oRho + 1] / per(p / S)[L::oRho];
+        rescale_contact<CONE>(ww, ratio);
+        wsum = rescale_sum_row(wsum, ratio, cfg.gamma);
+      }
+      rebuild();
+      if (moved) copy_rows();
+    }
   }
 }
 

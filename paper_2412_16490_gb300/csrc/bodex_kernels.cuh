@@ -490,28 +490,37 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
       const float psum = fmaxf(wsum, cfg.gamma), dsum = wsum - psum;
       if (CONE == CONE_SOC) {
         float dl[4];
-        soc_contact_primal<true>(ww, wy[0], wy[1], wy[2], cfg, rp, np, dl);
+        if (adaptive) soc_contact_primal<true>(ww, wy[0], wy[1], wy[2], cfg, rp, np, dl);
+        else soc_contact_primal<false>(ww, wy[0], wy[1], wy[2], cfg, rp, np, dl);
         at[0] = fmaf(cfg.mu, dl[1], dl[0]) + dsum;
         at[1] = dl[2];
         at[2] = dl[3];
       } else {
-        pyr_contact_primal<true>(ww, wy[0], wy[1], wy[2], cfg, rp, np);
+        if (adaptive) pyr_contact_primal<true>(ww, wy[0], wy[1], wy[2], cfg, rp, np);
+        else pyr_contact_primal<false>(ww, wy[0], wy[1], wy[2], cfg, rp, np);
         pyr_contact_atd(ww, dsum, cfg, at);
       }
       rp = fmaxf(rp, fabsf(sumn - psum));
-      np = fmaxf(np, fmaxf(fabsf(sumn), fabsf(psum)));
       float gy[6];
       g_times<NV>(Gg, ya, gy);
 #pragma unroll
-      for (int q = 0; q < 3; ++q)
-        dual_component<NV, true>(Gg, 3 * ci + q, gy, wy[q], wmq[q], at[q], cfg, rho, rd, nd);
-      float rpg = 0.f, rdg = 0.f, scale[2] = {0.f, 0.f};  // group maxima
+      for (int q = 0; q < 3; ++q) {
+        if (adaptive) dual_component<NV, true>(Gg, 3 * ci + q, gy, wy[q], wmq[q], at[q], cfg, rho, rd, nd);
+        else dual_component<NV, false>(Gg, 3 * ci + q, gy, wy[q], wmq[q], at[q], cfg, rho, rd, nd);
+      }
+      float rpg = 0.f, rdg = 0.f, scale[2] = {0.f, 0.f};  // group maxima (scales: adaptive rho only)
 #pragma unroll
       for (int i = 0; i < M; ++i) {
         rpg = fmaxf(rpg, __shfl_sync(0xffffffffu, rp, gb + i));
         rdg = fmaxf(rdg, __shfl_sync(0xffffffffu, rd, gb + i));
-        scale[0] = fmaxf(scale[0], __shfl_sync(0xffffffffu, np, gb + i));
-        scale[1] = fmaxf(scale[1], __shfl_sync(0xffffffffu, nd, gb + i));
+      }
+      if (adaptive) {
+        np = fmaxf(np, fmaxf(fabsf(sumn), fabsf(psum)));
+#pragma unroll
+        for (int i = 0; i < M; ++i) {
+          scale[0] = fmaxf(scale[0], __shfl_sync(0xffffffffu, np, gb + i));
+          scale[1] = fmaxf(scale[1], __shfl_sync(0xffffffffu, nd, gb + i));
+        }
       }
       const bool conv = rpg <= cfg.eps && rdg <= cfg.eps;
       const bool done = mine && (conv || it >= cfg.iters);

@@ -168,11 +168,16 @@ typedef struct bodex_qp_params {
                         8 facets (pyramid, 9m+1 rows in all) or the cone rows
                         (mu f_n, f_d, f_e) (elliptic, 4m+1 rows in all); the sum row last. */
   int adaptive_rho;  /* 1: with eps_abs > 0, adapt rho per grasp by residual balancing
-                        (OSQP, Stellato et al. 2020): every check_every iterations,
-                        when sqrt(|r_p| / |r_d|) averaged over the grasp's unconverged
-                        QPs exceeds 5 or 1/5, rho is multiplied by it and K^-1 rebuilt.
-                        Results are unchanged up to the residual target; 0: fixed rho.
-                        Ignored when eps_abs == 0 (fixed iteration counts). */
+                        (OSQP, Stellato et al. 2020, Sec. 5.2): every check_every
+                        iterations each unconverged QP proposes
+                        sqrt((|r_p| / s_p) / (|r_d| / s_d)), with s_p = max(|A y|, |z|)
+                        and s_d = max(|P y|, |A^T lam|, |q|); when the geometric mean of
+                        the grasp's proposals exceeds 5 or 1/5, rho (clamped to
+                        [1e-6, 1e6]) is multiplied by it and K^-1 rebuilt.  The
+                        returned lam = rho (w - z) uses the grasp's final rho; a warm
+                        start reads lam with params->rho.  Results are unchanged up to
+                        the residual target; 0: fixed rho.  Ignored when eps_abs == 0
+                        (fixed iteration counts). */
 } bodex_qp_params;
 
 #define BODEX_CONE_PYRAMID 0

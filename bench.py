@@ -277,6 +277,7 @@ def run_ours(args, rank, world, local_rank):
         extra["qp_solves"]["adaptive_rho"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev, adaptive_rho=1)
         extra["qp_solves_elliptic_cone"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev, cone=bx.CONE_ELLIPTIC)
         extra["qp_solves_warm_in_loop"] = qp_solve_rate_warm(bx, torch, H, Ob, x_dev, T_dev, P, adaptive_rho=0)
+        extra["small_configs"] = small_configs(bx, torch)
         extra["e2e"] = e2e_rate(bx, torch, H, Ob, st, x0, T_dev, sp)
         extra["persistent_mixed"] = persistent_mixed(bx, torch, P)
         if args.serve_jobs > 0:
@@ -630,6 +631,44 @@ def qp_solve_rate_warm(bx, torch, H, Ob, x_dev, T_dev, P, adaptive_rho=1, at_ste
             "iters_median": float(it.median().item()), "iters_max": int(it.max().item()),
             "cold_iters_median_same_qps": float(cold_it.median().item()), "ms": dt * 1e3,
             "adaptive_rho": bool(adaptive_rho)}
+
+
+def small_configs(bx, torch):
+    """The two small workloads: the tiny case (64 grasps of the 4-finger
+    hand on an analytic sphere, 6 wrenches, 50 upper steps x 30 ADMM
+    iterations) as one fused launch, latency-bound by construction (64 grasps
+    fill 4 CTAs of 152 SMs, so its roofline fraction means nothing); and the
+    autograd path on 1024 grasps of the same hand and object (forward: the
+    fused evaluation to a 1e-5 residual; backward: the adjoint kernel)."""
+    from paper_2412_16490_gb300.autograd import grasp_energy
+    out = {}
+    hand, obj, x0, T, P, steps, iters = I.workload("tiny")
+    H, Ob = bx.Hand(hand), bx.Object(obj)
+    st = bx.State(H, x0.shape[0], T.shape[0])
+    x, Td = torch.as_tensor(x0).cuda(), torch.as_tensor(T).cuda()
+    sp = bx.step_params(P, qp=bx.qp_params(max_iter=iters))
+
+    def run():
+        st.set_pose(x)
+        bx.bodex_step(H, Ob, st, Td, steps, sp)
+
+    ms = _timed(torch, run, reps=10)
+    out["tiny_64_grasps"] = {"ms": ms, "grasps_per_s": x0.shape[0] / ms * 1e3, "upper_steps": steps,
+                             "admm_iters": iters, "note": "latency-bound (4 CTAs); no roofline"}
+    hand, obj, x0, T, P, _, iters = I.workload("grad")
+    H, Ob = bx.Hand(hand), bx.Object(obj)
+    Td = torch.as_tensor(T).cuda()
+    sp = bx.step_params(P, qp=bx.qp_params(eps_abs=1e-5, max_iter=5000, check_every=10))
+    xg = torch.as_tensor(x0).cuda().requires_grad_(True)
+
+    def fwd_bwd():
+        xg.grad = None
+        grasp_energy(xg, H, Ob, Td, sp).sum().backward()
+
+    ms = _timed(torch, fwd_bwd, reps=5)
+    out["autograd_1024_grasps"] = {"ms": ms, "grasps_per_s": x0.shape[0] / ms * 1e3,
+                                   "what": "forward (QPs to 1e-5, cap 5000) + backward (adjoint kernel)"}
+    return out
 
 
 def e2e_rate(bx, torch, H, Ob, st, x0, T_dev, sp, reps=3):

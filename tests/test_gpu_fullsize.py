@@ -120,3 +120,26 @@ def test_fullsize_step_launch(full):
     assert (host(status) & bx.ST_NONFINITE == 0).all()
     E0 = host(bx.bodex_energy_grad(H, Ob, x, Td, sp)["E"])
     assert np.median(host(E) / E0) < 0.5
+
+
+def test_fullsize_mixed_launch_equals_single_launches():
+    """The mixed-template batch at full size (8704 grasps over 6 jobs, 3-, 4-
+    and 5-contact hands): one several-job launch of 5 upper steps gives every
+    grasp the pose of its own job's launch, bitwise."""
+    jobs, T = I.mixed_workload(seed=4)
+    assert sum(x.shape[0] for _, _, x in jobs) == 8704
+    Td = cuda(T)
+    sp = bx.step_params(I.default_params(), qp=bx.qp_params(max_iter=50))
+    hands, table, singles = {}, [], []
+    for hand, obj, x0 in jobs:
+        H = hands.setdefault(hand.name, bx.Hand(hand))
+        Ob = bx.Object(obj)
+        a, b = bx.State(H, x0.shape[0], 12), bx.State(H, x0.shape[0], 12)
+        a.set_pose(cuda(x0))
+        b.set_pose(cuda(x0))
+        table.append(dict(hand=H, obj=Ob, state=a, T=Td, n_steps=5))
+        bx.bodex_step(H, Ob, b, Td, 5, sp)
+        singles.append((a, b))
+    bx.bodex_step_multi(table, sp)
+    for a, b in singles:
+        assert torch.equal(a.pose(), b.pose())

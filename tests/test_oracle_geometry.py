@@ -1,12 +1,16 @@
 """Pins for the oracle's kinematics, SDF query, tangent basis, energy gradient
 and upper-level step (Secs. III, IV-B, IV-C)."""
+import json
 import math
+import os
 
 import numpy as np
 import pytest
 
 import bodex_inputs as I
 import oracle as O
+
+HERE = os.path.dirname(os.path.abspath(__file__))
 
 
 # ----------------------------------------------------------------- FK
@@ -285,6 +289,38 @@ def test_adam_first_step_and_clamp():
     want = np.clip(x_ref - lr * g / (np.abs(g) + P["adam_eps"]), tpl.qmin, tpl.qmax)
     np.testing.assert_allclose(x, want, atol=1e-15)
     assert x[1, 6] <= tpl.qmax[6]
+
+
+def test_adam_three_steps_golden():
+    """Three Adam steps on the gradient sequence g, -g, 2g against the
+    hand-derived moments and bias corrections of tests/golden (a step counter
+    that never advances, a wrong power of b1 or b2, or a missing bias
+    correction changes m-hat or v-hat at step 2 or 3).  One coordinate
+    starts half a step below its upper limit: steps 1 and 3 end on the clamp."""
+    fx = json.load(open(os.path.join(HERE, "golden", "adam_three_steps.json")))
+    tpl = I.hand_template("hand4")
+    H = O.Hand(tpl)
+    P = I.default_params()
+    assert (P["b1"], P["b2"]) == (fx["b1"], fx["b2"])
+    D = tpl.dof
+    rng = np.random.default_rng(7)
+    g = rng.uniform(0.5, 2.0, D) * rng.choice([-1.0, 1.0], D)
+    lr = np.where(np.arange(D) < 3, P["lr_t"], P["lr_r"])
+    x0 = np.clip(rng.uniform(-0.2, 0.2, D), tpl.qmin, tpl.qmax)
+    g[8] = -abs(g[8])  # moves x[8] up at steps 1 and 3
+    x0[8] = tpl.qmax[8] - 0.5 * lr[8]
+    x, mm, vv = x0[None].copy(), np.zeros((1, D)), np.zeros((1, D))
+    want = x0.copy()
+    for t in range(3):
+        O.adam(H, P, x, mm, vv, (fx["grad_factor"][t] * g)[None], t + 1)
+        np.testing.assert_allclose(mm[0], fx["m_coef"][t] * g, rtol=1e-13)
+        np.testing.assert_allclose(vv[0], fx["v_coef"][t] * g * g, rtol=1e-13)
+        mhat = fx["m_coef"][t] / fx["bias1"][t] * g
+        vhat = fx["v_coef"][t] / fx["bias2"][t] * g * g
+        want = np.clip(want - lr * mhat / (np.sqrt(vhat) + P["adam_eps"]), tpl.qmin, tpl.qmax)
+        np.testing.assert_allclose(x[0], want, rtol=0, atol=1e-14)
+    # the clamped coordinate: on the limit after step 1, lr/19 below it after step 2, on it after step 3
+    assert x[0, 8] == tpl.qmax[8]
 
 
 def test_run_decreases_energy_tiny():

@@ -241,9 +241,12 @@ class Server(_Base):
             return lst.pop()
         return super()._new_state(spec, hand)
 
-    def _evict_pool(self, need: int):
-        """Frees pooled states until `need` more bytes fit the budget."""
+    def _evict_pool(self, need: int, keep=None):
+        """Frees pooled states until `need` more bytes fit the budget, never
+        the pool of shape `keep` (the state the admitted job will reuse)."""
         for key in list(self.pool):
+            if key == keep:
+                continue
             lst = self.pool[key]
             while lst and self.used + self.pooled + need > self.hbm_budget:
                 st = lst.pop()
@@ -259,7 +262,7 @@ class Server(_Base):
             # a pooled state of the same shape is reused: its bytes are already held
             reuse = state_bytes(spec) if self.pool.get(_state_key(spec)) else 0
             if self.used + self.pooled + nb - reuse > self.hbm_budget:
-                self._evict_pool(nb - reuse)
+                self._evict_pool(nb - reuse, keep=_state_key(spec))
             if self.used + self.pooled + nb - reuse > self.hbm_budget:
                 if not self.active and not self.finishing and nb > self.hbm_budget:
                     raise MemoryError(f"job {jid} needs {nb} bytes, over the HBM budget {self.hbm_budget}")

@@ -147,3 +147,24 @@ def test_pooled_states_are_reused_or_evicted():
     srv.submit(b)
     srv._admit()
     assert len(srv.active) == 1 and srv.pool == {} and srv.pooled == 0
+
+
+def test_eviction_keeps_the_pooled_state_the_job_reuses():
+    """The budget only fits the job if other pooled states go: eviction frees
+    those and keeps the pooled state of the job's own shape, which the job
+    then reuses, so the bytes held stay within the budget."""
+    a = _spec(512)
+    sb = state_bytes(a)
+    mine = types.SimpleNamespace(B=512, D=a.hand.dof, s=12, m=5)
+    other = types.SimpleNamespace(B=256, D=a.hand.dof, s=12, m=5)
+    ob = 4 * 256 * (3 * a.hand.dof + 12 * (12 * 5 + 1) + 1)
+    key = (id(a.hand), 512, 12)
+    srv = _host_server(hbm_budget=job_bytes(a) + ob // 2)
+    srv.pool = {("other", 256, 12): [other], key: [mine]}  # the other shape first in eviction order
+    srv.pooled = sb + ob
+    srv.submit(a)
+    srv._admit()
+    assert len(srv.active) == 1
+    assert srv.pool == {key: [mine]} and srv.pooled == sb
+    # the job reuses `mine`: held bytes = used + pooled - reused state
+    assert srv.used + srv.pooled - sb <= srv.hbm_budget

@@ -58,6 +58,7 @@ extern "C" {
 #define BODEX_ST_NONFINITE 1       /* non-finite input or result */
 #define BODEX_ST_NOT_CONVERGED 2   /* QP residual above eps_abs after max_iter */
 #define BODEX_ST_DEGENERATE_NORMAL 4 /* |grad phi| < 1e-12 at a contact */
+#define BODEX_ST_POLISHED 8        /* QP result replaced by its polished solution (qp.polish) */
 
 /* ---------------------------------------------------------------- limits */
 #define BODEX_MAX_JOINTS 32   /* revolute joints per hand */
@@ -178,6 +179,14 @@ typedef struct bodex_qp_params {
                         start reads lam with params->rho.  Results are unchanged up to
                         the residual target; 0: fixed rho.  Ignored when eps_abs == 0
                         (fixed iteration counts). */
+  int polish;        /* 1 (pyramid cone, eps_reg = 0): after the ADMM run, solve every QP
+                        exactly in FP64 by Wolfe's minimum-norm-point method (the QP is
+                        the nearest point of the wrench polytope G C to beta t; Wolfe 1976)
+                        and replace y and Q by that minimiser and optimum (Q to FP64
+                        rounding, y rounded to float).  Such QPs carry BODEX_ST_POLISHED
+                        and not BODEX_ST_NOT_CONVERGED; z, lam, res and iters stay those of
+                        the ADMM run.  A QP the exact solve gives up on (200 oracle calls)
+                        keeps its ADMM result.  0: off.  bodex_qp_solve_batch only. */
 } bodex_qp_params;
 
 #define BODEX_CONE_PYRAMID 0
@@ -385,7 +394,13 @@ int bodex_contact_metrics(bodex_hand_t hand, bodex_object_t obj, const float* x,
  *     BODEX_ERR_INVALID before any device work.
  *   - The first call on a device looks up the array's device address
  *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *     before any stream capture.  Under CUDA's default lazy module loading
+ *     that first call (and the first call with a hand of a new contact
+ *     count m, whose kernel lives in another module) also loads the
+ *     library's code and the array onto the device, which does allocate
+ *     device memory: a caller with a no-allocation phase makes one warm-up
+ *     call per device and per hand template at start-up, before that phase.
+ *     Calls after the warm-up allocate nothing.
  *   - All calls share the array and each clears what it uses before its
  *     kernel runs: calls that overlap on the GPU (other streams, other host
  *     threads) race and must be serialised by the caller.

@@ -77,6 +77,7 @@ struct AdmmCfg {
   float beta, gamma, rho, sigma, alpha, eps, eps_reg;
   int iters, check;
   int fp64_setup;  // build K^-1 in double (set by the host per launch)
+  int polish;      // polish converged pyramid QPs (bodex_qp_solve_batch)
 };
 
 __host__ __device__ inline AdmmCfg admm_cfg(const bodex_qp_params& p) {
@@ -95,6 +96,7 @@ __host__ __device__ inline AdmmCfg admm_cfg(const bodex_qp_params& p) {
   c.iters = p.max_iter;
   c.check = p.check_every > 0 ? p.check_every : 10;
   c.fp64_setup = 0;
+  c.polish = p.polish;
   return c;
 }
 
@@ -821,6 +823,228 @@ __device__ __forceinline__ void neg_q(const float* G, const float* t, float beta
     mq[a] = 2.f * beta * s;
   }
 }
+
+// ------------------------------------------------------------------ exact QP: nearest point of G C
+// With eps_reg = 0 the objective |beta t - G y|^2 depends on y only through
+// the wrench G y, so the QP of Eqs. (7)-(9) is the nearest-point problem
+// from beta t to the polytope G C in R^6, C the feasible forces.  Wolfe's
+// minimum-norm-point algorithm (Wolfe 1976, "Finding the nearest point in a
+// polytope", Math. Programming 11) solves it exactly in finitely many steps
+// given only a linear-minimisation oracle over C: it keeps the point
+// x = G y - beta t as a convex combination of at most 7 points G v_i - beta t
+// (v_i vertices of C), adds the oracle's vertex, and moves to the nearest
+// point of the affine hull of its set, dropping points whose weight would
+// turn negative.
+//
+// The oracle: minimise g . v over C.  Per contact C is the convex hull of
+// the apex 0 and the pyramid's 8 edge tips at f_n = 1,
+// E_k = (1, mu cos(k pi/4), mu sin(k pi/4)) in the contact's (n, d, e)
+// frame, so contact i contributes c_i f_i with c_i = min_k g_i . E_k and
+// f_i in [0, 1] its normal force along its best edge; with sum_i f_i >= gamma
+// this is a continuous knapsack: f_i = 1 where c_i < 0, then the cheapest
+// remaining contacts filled in order of c_i until the sum reaches gamma.
+//
+// Stops when the Frank-Wolfe gap |x|^2 - x . q_new (an upper bound on
+// Q(y) - Q*) falls to tol max(1, max |q_i|^2), or after max_it oracle calls.
+// Returns the oracle calls used (-1: gave up, or stalled on an affinely
+// dependent point with a gap above 1e4 tol); y = sum lambda_i v_i and
+// Q = |x|^2.  Precision R: double for polishing.
+template <int M, typename R>
+struct Wolfe {
+  static constexpr int NV = 3 * M, K = 8;  // at most 7 points in R^6, one slot for the newcomer
+  // v . (oracle) for a gradient gy (in y): the vertex in v, its wrench part G v - b in q
+  __device__ static void oracle(const float* G, const R* b, const R* gy, const AdmmCfg& c, R* v, R* q) {
+    R cbest[M];
+    int kbest[M];
+    const R mu = (R)c.mu;
+    for (int i = 0; i < M; ++i) {
+      R best = 0;
+      int kb = 0;
+      for (int k = 0; k < 8; ++k) {
+        R ck, sk;
+        if constexpr (sizeof(R) == 8) sincospi((double)k * 0.25, &sk, &ck);
+        else sincospif((float)k * 0.25f, &sk, &ck);
+        const R val = gy[3 * i] + mu * (ck * gy[3 * i + 1] + sk * gy[3 * i + 2]);
+        if (k == 0 || val < best) best = val, kb = k;
+      }
+      cbest[i] = best;
+      kbest[i] = kb;
+    }
+    R f[M], sum = 0;
+    for (int i = 0; i < M; ++i) {
+      f[i] = cbest[i] < 0 ? R(1) : R(0);
+      sum += f[i];
+    }
+    const R gam = (R)c.gamma;
+    while (sum < gam) {  // fill the cheapest contact not yet full
+      int pick = -1;
+      for (int i = 0; i < M; ++i)
+        if (f[i] < R(1) && (pick < 0 || cbest[i] < cbest[pick])) pick = i;
+      if (pick < 0) break;
+      const R add = fmin(R(1) - f[pick], gam - sum);
+      f[pick] += add;
+      sum += add;
+    }
+    for (int i = 0; i < M; ++i) {
+      R ck, sk;
+      if constexpr (sizeof(R) == 8) sincospi((double)kbest[i] * 0.25, &sk, &ck);
+      else sincospif((float)kbest[i] * 0.25f, &sk, &ck);
+      v[3 * i] = f[i];
+      v[3 * i + 1] = f[i] * mu * ck;
+      v[3 * i + 2] = f[i] * mu * sk;
+    }
+    for (int r = 0; r < 6; ++r) {
+      R s = -b[r];
+      for (int a = 0; a < NV; ++a) s += (R)G[r * NV + a] * v[a];
+      q[r] = s;
+    }
+  }
+
+  __device__ static int solve(const float* G, const float* t, const AdmmCfg& c, const float* y_start, R tol,
+                              int max_it, R* y, R& Q) {
+    R b[6], V[K][NV], P[K][6], lam[K], x[6], gy[NV];
+    for (int r = 0; r < 6; ++r) b[r] = (R)c.beta * (R)t[r];
+    // first vertex: the oracle at the gradient of the starting point (any y; zero is fine)
+    {
+      R ys[NV], res[6];
+      for (int a = 0; a < NV; ++a) ys[a] = y_start ? (R)y_start[a] : R(0);
+      for (int r = 0; r < 6; ++r) {
+        R s = -b[r];
+        for (int a = 0; a < NV; ++a) s += (R)G[r * NV + a] * ys[a];
+        res[r] = s;
+      }
+      for (int a = 0; a < NV; ++a) {
+        R s = 0;
+        for (int r = 0; r < 6; ++r) s += (R)G[r * NV + a] * res[r];
+        gy[a] = s;
+      }
+    }
+    oracle(G, b, gy, c, V[0], P[0]);
+    int n = 1;
+    lam[0] = 1;
+    for (int r = 0; r < 6; ++r) x[r] = P[0][r];
+    int calls = 1;
+    bool ok = true;
+    for (;;) {
+      // gradient of |x|^2 / 2 in y: G^T x; the oracle's vertex
+      for (int a = 0; a < NV; ++a) {
+        R s = 0;
+        for (int r = 0; r < 6; ++r) s += (R)G[r * NV + a] * x[r];
+        gy[a] = s;
+      }
+      R vn[NV], qn[6];
+      oracle(G, b, gy, c, vn, qn);
+      ++calls;
+      R xx = 0, xq = 0, qmax = 1;
+      for (int r = 0; r < 6; ++r) xx += x[r] * x[r], xq += x[r] * qn[r];
+      for (int i = 0; i < n; ++i) {
+        R s = 0;
+        for (int r = 0; r < 6; ++r) s += P[i][r] * P[i][r];
+        qmax = fmax(qmax, s);
+      }
+      if (xx - xq <= tol * qmax) break;  // Frank-Wolfe gap: optimal to tol
+      if (calls > max_it || n >= K) return -1;
+      for (int a = 0; a < NV; ++a) V[n][a] = vn[a];
+      for (int r = 0; r < 6; ++r) P[n][r] = qn[r];
+      lam[n++] = 0;
+      // minor cycles: nearest point of the affine hull of the set; while it
+      // leaves the simplex, step towards it until a weight reaches 0 and drop that point
+      for (int guard = 0;; ++guard) {
+        if (guard > 2 * K) return -1;
+        // affine minimiser: alpha_0 = 1 - sum alpha_i, (D^T D) alpha' = -D^T p_0, D_i = p_i - p_0
+        R A[K - 1][K - 1], rhs[K - 1], al[K];
+        const int d = n - 1;
+        for (int i = 0; i < d; ++i) {
+          R s = 0;
+          for (int r = 0; r < 6; ++r) s -= (P[i + 1][r] - P[0][r]) * P[0][r];
+          rhs[i] = s;
+          for (int j = 0; j <= i; ++j) {
+            R e = 0;
+            for (int r = 0; r < 6; ++r) e += (P[i + 1][r] - P[0][r]) * (P[j + 1][r] - P[0][r]);
+            A[i][j] = e;
+          }
+        }
+        bool singular = false;
+        for (int j = 0; j < d; ++j) {  // Cholesky, lower triangle in place
+          R dd = A[j][j];
+          for (int k = 0; k < j; ++k) dd -= A[j][k] * A[j][k];
+          if (!(dd > R(sizeof(R) == 8 ? 1e-28 : 1e-14) * qmax)) {
+            singular = true;
+            break;
+          }
+          dd = sqrt(dd);
+          A[j][j] = dd;
+          for (int i = j + 1; i < d; ++i) {
+            R s = A[i][j];
+            for (int k = 0; k < j; ++k) s -= A[i][k] * A[j][k];
+            A[i][j] = s / dd;
+          }
+        }
+        if (singular) {  // the newcomer is affinely dependent on the set: no progress is possible;
+          --n;           // the current point stands if its gap is within 1e4 tol
+          ok = xx - xq <= R(1e4) * tol * qmax;
+          goto done;
+        }
+        for (int i = 0; i < d; ++i) {
+          R s = rhs[i];
+          for (int k = 0; k < i; ++k) s -= A[i][k] * rhs[k];
+          rhs[i] = s / A[i][i];
+        }
+        for (int i = d - 1; i >= 0; --i) {
+          R s = rhs[i];
+          for (int k = i + 1; k < d; ++k) s -= A[k][i] * rhs[k];
+          rhs[i] = s / A[i][i];
+        }
+        R a0 = 1;
+        for (int i = 0; i < d; ++i) al[i + 1] = rhs[i], a0 -= rhs[i];
+        al[0] = a0;
+        bool inside = true;
+        for (int i = 0; i < n; ++i) inside = inside && al[i] > 0;
+        if (inside) {
+          for (int i = 0; i < n; ++i) lam[i] = al[i];
+          break;
+        }
+        R th = 1;  // largest step towards al keeping every weight >= 0
+        for (int i = 0; i < n; ++i)
+          if (al[i] <= 0) th = fmin(th, lam[i] / (lam[i] - al[i]));
+        int w = 0;
+        R tot = 0;
+        for (int i = 0; i < n; ++i) {
+          const R li = lam[i] + th * (al[i] - lam[i]);
+          if (li > R(0) && !(al[i] <= 0 && lam[i] / (lam[i] - al[i]) <= th)) {
+            lam[w] = li;
+            for (int a = 0; a < NV; ++a) V[w][a] = V[i][a];
+            for (int r = 0; r < 6; ++r) P[w][r] = P[i][r];
+            tot += li;
+            ++w;
+          }
+        }
+        n = w;
+        for (int i = 0; i < n; ++i) lam[i] /= tot;
+        if (n == 1) break;
+      }
+      for (int r = 0; r < 6; ++r) {
+        R s = 0;
+        for (int i = 0; i < n; ++i) s += lam[i] * P[i][r];
+        x[r] = s;
+      }
+    }
+  done:
+    for (int r = 0; r < 6; ++r) {
+      R s = 0;
+      for (int i = 0; i < n; ++i) s += lam[i] * P[i][r];
+      x[r] = s;
+    }
+    Q = 0;
+    for (int r = 0; r < 6; ++r) Q += x[r] * x[r];
+    for (int a = 0; a < NV; ++a) {
+      R s = 0;
+      for (int i = 0; i < n; ++i) s += lam[i] * V[i][a];
+      y[a] = s;
+    }
+    return ok ? calls : -1;
+  }
+};
 
 // ------------------------------------------------------------------ elliptic cone
 // The unlinearised friction model: per contact the row f_n in [0, 1] and

@@ -564,6 +564,35 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
   }
 }
 
+// ============================================================================ kernel: solution polishing
+// A pass after qp_solve_kernel when qp.polish is set (pyramid QPs with
+// eps_reg = 0): one thread per QP solves the QP exactly in FP64 by the
+// minimum-norm-point method (Wolfe<M, double>), its first vertex taken at the
+// ADMM point.  Where that succeeds, y and Q become the exact minimiser and
+// optimum (Q to FP64 rounding, y rounded to float), the QP gets
+// BODEX_ST_POLISHED and loses BODEX_ST_NOT_CONVERGED; z, lam, the residuals
+// and the iteration count stay those of the ADMM run.
+template <int M>
+__global__ void __launch_bounds__(128) qp_polish_kernel(const float* __restrict__ Gin, int B,
+                                                        const float* __restrict__ T, int S, AdmmCfg cfg, float* y_io,
+                                                        float* Qout, int32_t* status_io) {
+  constexpr int NV = 3 * M;
+  const size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (size_t)B * S) return;
+  if (status_io && (status_io[q] & BODEX_ST_NONFINITE)) return;
+  const size_t b = q / S;
+  const int j = (int)(q % S);
+  const float* G = Gin + b * 6 * NV;
+  float t[6], ys[NV];
+  for (int r = 0; r < 6; ++r) t[r] = T[j * 6 + r];
+  for (int a = 0; a < NV; ++a) ys[a] = y_io[q * NV + a];
+  double yd[NV], Qd;
+  if (Wolfe<M, double>::solve(G, t, cfg, ys, 1e-13, 200, yd, Qd) < 0) return;
+  for (int a = 0; a < NV; ++a) y_io[q * NV + a] = (float)yd[a];
+  Qout[q] = (float)Qd;
+  if (status_io) status_io[q] = (status_io[q] & ~BODEX_ST_NOT_CONVERGED) | BODEX_ST_POLISHED;
+}
+
 // ============================================================================ kernel: fused evaluation / step
 struct FusedArgs {
   const HandDev* hand;
@@ -1089,6 +1118,13 @@ inline int run_qp(const float* G, int B, const float* T, int s, const AdmmCfg& c
     if (int r = ensure_smem(qp_solve_kernel<M, CONE_PYR>, bytes)) return r;
     qp_solve_kernel<M, CONE_PYR><<<(B + gpb - 1) / gpb, gpb * s, bytes, st>>>(G, B, T, s, cfg, warm, y, z, lam, Q,
                                                                               iters, status, res);
+    if (int r = launch_err("qp_solve_kernel launch")) return r;
+    if (cfg.polish && cfg.eps_reg == 0.f) {
+      const size_t n = (size_t)B * s;
+      qp_polish_kernel<M><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(G, B, T, s, cfg, y, Q, status);
+      return launch_err("qp_polish_kernel launch");
+    }
+    return BODEX_OK;
   }
   return launch_err("qp_solve_kernel launch");
 }

@@ -16,7 +16,9 @@ pytestmark = pytest.mark.gpu
 def grad_case():
     hand, obj, x0, T, P, _, _ = I.workload("grad")
     P = dict(P, eps_reg=1e-3)
-    sp = bx.step_params(P, qp=bx.qp_params(eps_abs=1e-6, eps_reg=1e-3, max_iter=20000, check_every=10))
+    # 2e-6: one QP of the 6144 (grasp 505, wrench 0) has its float32 dual-residual
+    # floor at 1.9e-6 and never reaches 1e-6; at 2e-6 every QP converges
+    sp = bx.step_params(P, qp=bx.qp_params(eps_abs=2e-6, eps_reg=1e-3, max_iter=100000, check_every=10))
     return hand, obj, x0, T, P, sp, bx.Hand(hand), bx.Object(obj)
 
 
@@ -30,12 +32,11 @@ def test_autograd_gradient_matches_oracle_differences(grad_case):
     idx = np.random.default_rng(3).choice(1024, 64, replace=False)
     gfd = O.grad_fd(O.Hand(hand), O.Object(obj), x0[idx].astype(np.float64), T, P, step=1e-6)
     rel = np.linalg.norm(g[idx] - gfd, axis=1) / np.maximum(np.linalg.norm(gfd, axis=1), 1e-3)
-    # the envelope gradient holds at the optimum: compare where every QP of
-    # the grasp reached the residual target (the forward's status bits)
-    st = host(bx.bodex_energy_grad(H, Ob, cuda(x0), cuda(T), sp)["status"])[idx]
-    ok = (st & bx.ST_NOT_CONVERGED) == 0
-    assert ok.mean() >= 0.9
-    assert (rel[ok] <= 1e-3).all(), np.sort(rel[ok])[-5:]
+    # the envelope gradient holds at the optimum: every QP of every grasp
+    # reached the residual target (the forward's status bits)
+    st = host(bx.bodex_energy_grad(H, Ob, cuda(x0), cuda(T), sp)["status"])
+    assert ((st & bx.ST_NOT_CONVERGED) == 0).all(), np.nonzero(st & bx.ST_NOT_CONVERGED)[0]
+    assert (rel <= 1e-3).all(), np.sort(rel)[-5:]
     assert np.median(rel) <= 1e-4
 
 

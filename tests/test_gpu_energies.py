@@ -84,12 +84,12 @@ def test_qp_baseline_beta_zero_matches_oracle():
     hand, obj, x0, T, P = _workload("tiny", 48)
     Pr = dict(P, beta=0.0, eps_reg=1e-3)
     H, Ob = bx.Hand(hand), bx.Object(obj)
-    sp = bx.step_params(Pr, qp=bx.qp_params(beta=0.0, eps_abs=1e-6, eps_reg=1e-3, max_iter=20000, check_every=10))
+    sp = bx.step_params(Pr, qp=bx.qp_params(beta=0.0, eps_abs=1e-6, eps_reg=1e-3, max_iter=100000, check_every=10))
     out = bx.bodex_energy_grad(H, Ob, cuda(x0), cuda(T), sp)
     ev = O.evaluate(O.Hand(hand), O.Object(obj), x0.astype(np.float64), T, Pr)
     st = host(out["status"])
     ok = (st & bx.ST_NOT_CONVERGED) == 0
-    assert ok.mean() >= 0.9
+    assert ok.all(), np.nonzero(~ok)[0]
     np.testing.assert_allclose(host(out["E"])[ok], ev["E"][ok], rtol=1e-4, atol=1e-6)
     g, gref = host(out["dEdx"]), ev["grad"]
     rel = np.linalg.norm(g - gref, axis=1) / np.maximum(np.linalg.norm(gref, axis=1), 1e-3)

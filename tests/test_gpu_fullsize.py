@@ -48,42 +48,52 @@ def test_fullsize_contacts_sampled(full):
 
 
 def test_fullsize_qp_batch_sampled(full):
-    """The bench's standalone QP configuration: all 49,152 QPs, cold start,
-    1e-5, cap 5000, with the G the GPU computes."""
+    """The bench's standalone QP configuration (all 49,152 QPs, cold start,
+    1e-5, cap 5000, with the G the GPU computes), polished: every QP gets the
+    exact FP64 solve, and the sampled grasps' values are within
+    1e-4 |Q*| + 1e-6 of the oracle's.  The ADMM run's own residuals: the
+    QPs it reports converged are at 1e-5, and on the sample their ADMM point
+    (y before polishing, from the same launch without polish) lies inside
+    its certificate around Q*."""
     hand, obj, x0, T, P, H, Ob = full
     G = bx.bodex_fk_contacts(H, Ob, cuda(x0))["G"]
-    out = bx.bodex_qp_solve_batch(G, cuda(T), bx.qp_params(mu=MU, beta=BETA, gamma=GAMMA, eps_abs=1e-5,
-                                                            max_iter=5000, check_every=10))
+    prm = bx.qp_params(mu=MU, beta=BETA, gamma=GAMMA, eps_abs=1e-5, max_iter=5000, check_every=10, polish=1)
+    out = bx.bodex_qp_solve_batch(G, cuda(T), prm)
     st = host(out["status"])
-    conv = (st & bx.ST_NOT_CONVERGED) == 0
-    assert (st & bx.ST_NONFINITE == 0).all() and conv.mean() > 0.99
-    res = host(out["res"])
-    assert (res[conv] <= 1e-5).all()
+    assert (st & bx.ST_NONFINITE == 0).all() and ((st & bx.ST_POLISHED) != 0).all()
     Gs = host(G)[SAMPLE].astype(np.float64)
-    y, z, lam = (host(out[k])[SAMPLE].astype(np.float64) for k in ("y", "z", "lam"))
     ref = O.qp_solve(Gs, T, mu=MU, beta=BETA, gamma=GAMMA, want_lam=True)
     assert (ref["status"] == 0).all()
+    y = host(out["y"])[SAMPLE].astype(np.float64)
     Qy = ((BETA * T[None].astype(np.float64) - np.einsum("bri,bsi->bsr", Gs, y)) ** 2).sum(-1)
-    np.testing.assert_allclose(host(out["Q"])[SAMPLE], Qy, rtol=1e-4, atol=1e-6)
-    lo, hi, rp, rd = qp_certificate(Gs, T.astype(np.float64), y, z, lam, np.abs(ref["lam"]).sum(-1), MU, BETA,
+    bar = 1e-4 * np.abs(ref["Q"]) + 1e-6
+    assert (np.abs(host(out["Q"])[SAMPLE] - ref["Q"]) <= bar).all()
+    assert (np.abs(Qy - ref["Q"]) <= bar).all()
+    # the same launch without polishing: ADMM's point and its certificate
+    prm.polish = 0
+    adm = bx.bodex_qp_solve_batch(G, cuda(T), prm)
+    conv = (host(adm["status"]) & bx.ST_NOT_CONVERGED) == 0
+    assert (host(adm["res"])[conv] <= 1e-5).all()
+    assert torch.equal(adm["iters"], out["iters"]) and torch.equal(adm["res"], out["res"])
+    ya, z, lam = (host(adm[k])[SAMPLE].astype(np.float64) for k in ("y", "z", "lam"))
+    Qa = ((BETA * T[None].astype(np.float64) - np.einsum("bri,bsi->bsr", Gs, ya)) ** 2).sum(-1)
+    lo, hi, rp, rd = qp_certificate(Gs, T.astype(np.float64), ya, z, lam, np.abs(ref["lam"]).sum(-1), MU, BETA,
                                     ref["y"])
-    d = Qy - ref["Q"]
+    d = Qa - ref["Q"]
     tol = 1e-4 * np.abs(ref["Q"]) + 1e-7
     assert (d >= lo - tol).all() and (d <= hi + tol).all()
-    cs = conv[SAMPLE]
-    assert np.abs(d[cs]).max() < 3e-4
-    assert (rp[cs] <= 2e-5).all() and (rd[cs] <= 2e-5).all()
 
 
 def test_fullsize_energy_gradient_sampled(full):
     hand, obj, x0, T, P, H, Ob = full
     Pr = dict(P, eps_reg=1e-3)
-    sp = bx.step_params(Pr, qp=bx.qp_params(eps_abs=1e-6, eps_reg=1e-3, max_iter=20000, check_every=10))
+    sp = bx.step_params(Pr, qp=bx.qp_params(eps_abs=1e-6, eps_reg=1e-3, max_iter=100000, check_every=10))
     out = bx.bodex_energy_grad(H, Ob, cuda(x0), cuda(T), sp)
     st = host(out["status"])
     assert (st & bx.ST_NONFINITE == 0).all() and np.isfinite(host(out["dEdx"])).all()
+    assert ((st & bx.ST_NOT_CONVERGED) == 0).all()  # every QP of all 4096 grasps reached 1e-6
     ev = O.evaluate(O.Hand(hand), O.Object(obj), x0[SAMPLE].astype(np.float64), T, Pr)
-    ok = ((st[SAMPLE] & bx.ST_NOT_CONVERGED) == 0) & _off_faces(obj, ev["c"]).all(-1)
+    ok = _off_faces(obj, ev["c"]).all(-1)  # queries within rounding of a voxel face may take the other cell
     assert ok.sum() >= len(SAMPLE) // 2
     np.testing.assert_allclose(host(out["E"])[SAMPLE][ok], ev["E"][ok], rtol=1e-4, atol=1e-6)
     g, gref = host(out["dEdx"])[SAMPLE], ev["grad"]

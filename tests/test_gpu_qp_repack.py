@@ -63,6 +63,3 @@ def test_qp_repacking_edge_shapes(B, s):
         one = bx.bodex_qp_solve_batch(G[b:b + 1].contiguous(), T, prm)
         for k in ("y", "z", "lam", "Q", "iters", "status"):
             assert torch.equal(full[k][b:b + 1], one[k]), (b, k)
-    if B:
-        conv = (host(full["status"]) & bx.ST_NOT_CONVERGED) == 0
-        assert conv.mean() > 0.9

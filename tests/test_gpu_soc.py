@@ -37,15 +37,19 @@ def test_soc_value_within_the_bracket_and_certificate(m, s, B):
     G32 = O.grasp_matrix(p, n).astype(np.float32)
     G = G32.astype(np.float64)
     ref = O.qp_soc(G, T, mu=MU, beta=BETA, gamma=GAMMA, K=K)
+    # the oracle's bracket solves QPs over pyramids of K = 256 facets (4m K rows):
+    # its active-set loop stalls on a few QPs here (status 1, no certificate:
+    # 1 of 204 on x86, 4 on Arm, whose libm rounds the facet angles
+    # differently); those have no exact reference and are left out
     ok = ref["status"] == 0
-    assert ok.mean() > 0.95
-    prm = bx.qp_params(mu=MU, beta=BETA, gamma=GAMMA, eps_abs=1e-5, max_iter=20000, check_every=10,
+    assert (~ok).sum() <= 5
+    prm = bx.qp_params(mu=MU, beta=BETA, gamma=GAMMA, eps_abs=1e-5, max_iter=100000, check_every=10,
                        cone=bx.CONE_ELLIPTIC)
     out = bx.bodex_qp_solve_batch(cuda(G32), cuda(T), prm)
     y, z, lam = (host(out[k]).astype(np.float64) for k in ("y", "z", "lam"))
     assert z.shape[-1] == 4 * m + 1
     conv = (host(out["status"]) & bx.ST_NOT_CONVERGED) == 0
-    assert conv.mean() > 0.95
+    assert conv.all(), [(i, host(out["res"])[i].tolist()) for i in zip(*np.nonzero(~conv))]
     # the kernel's y satisfies the cone up to its primal residual
     fn, ft = y[..., 0::3], np.hypot(y[..., 1::3], y[..., 2::3])
     assert (ft - MU * fn)[conv].max() < 1e-4
@@ -84,8 +88,9 @@ def test_soc_forces_on_the_regularised_problem():
     prm = bx.qp_params(eps_abs=2e-6, eps_reg=1e-3, max_iter=150000, check_every=10, cone=bx.CONE_ELLIPTIC)
     out = bx.bodex_qp_solve_batch(cuda(G32), cuda(T), prm)
     y = host(out["y"])
-    conv = ((host(out["status"]) & bx.ST_NOT_CONVERGED) == 0) & (ref["status"] == 0)
-    assert conv.mean() >= 0.95
+    assert (ref["status"] == 0).all()
+    conv = (host(out["status"]) & bx.ST_NOT_CONVERGED) == 0
+    assert conv.all(), [(i, host(out["res"])[i].tolist()) for i in zip(*np.nonzero(~conv))]
     assert np.abs(y - ref["y"])[conv].max() <= 2e-3
     r_gpu = T[None] - np.einsum("bri,bsi->bsr", G, y)
     r_ref = T[None] - np.einsum("bri,bsi->bsr", G, ref["y"])
@@ -108,7 +113,7 @@ def test_soc_energy_gradient_and_step_in_the_fused_kernel():
                     dict(Pr, cone=O.CONE_ELLIPTIC, cone_facets=2048))
     st = host(out["status"])
     ok = (st & bx.ST_NOT_CONVERGED) == 0
-    assert ok.mean() >= 0.9
+    assert ok.all(), np.nonzero(~ok)[0]
     np.testing.assert_allclose(host(out["E"])[ok], ev["E"][ok], rtol=2e-4, atol=1e-6)
     g, gref = host(out["dEdx"]), ev["grad"]
     rel = np.linalg.norm(g - gref, axis=1) / np.maximum(np.linalg.norm(gref, axis=1), 1e-3)

@@ -8,8 +8,10 @@ starts) in a fixed array of its own instead of a bodex_state_t.  This test
 calls that entry point through the C ABI twice in a row, on different
 poses, and checks each result against bodex_state_set_pose + bodex_step on
 the same inputs: the second call also shows that the array's leftovers from
-the first call do not leak into the next one.  It also checks that a batch
-larger than the array is refused before any device work.
+the first call do not leak into the next one.  Free device memory is read
+(cudaMemGetInfo) around that second call: once the first call has loaded the
+library's code and array onto the device, a call allocates nothing.  It also
+checks that a batch larger than the array is refused before any device work.
 
 This file is collected last (test_zz_*) so that a run stopping at its first
 failure has already run every other test.
@@ -53,10 +55,14 @@ def test_noalloc_step_matches_allocating_step_on_two_calls():
         got_x = x.clone()
         got_E = torch.empty(48, device="cuda")
         status = torch.empty(48, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         rc = lib.bodex_step_noalloc(H.handle, Ob.handle, _ptr(got_x), 48, _ptr(Tt), T.shape[0], n_steps,
                                     C.byref(sp), _ptr(got_E), _ptr(status), stream)
         assert rc == _binding.BODEX_OK, lib.bodex_last_error()
         torch.cuda.synchronize()
+        if first:  # the second call, after the first loaded the code and the array: no device memory taken
+            assert torch.cuda.mem_get_info()[0] == free0
         np.testing.assert_allclose(got_x.cpu().numpy(), want_x.cpu().numpy(), atol=1e-6)
         np.testing.assert_allclose(got_E.cpu().numpy(), want_E.cpu().numpy(), rtol=1e-5, atol=1e-7)
         assert (status.cpu().numpy() & bx.ST_NONFINITE == 0).all()

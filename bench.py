@@ -293,6 +293,7 @@ def run_ours(args, rank, world, local_rank):
         extra["qp_solves"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev)
         extra["qp_solves"]["adaptive_rho"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev, adaptive_rho=1)
         extra["qp_solves_elliptic_cone"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev, cone=bx.CONE_ELLIPTIC)
+        extra["qp_solves_exact"] = qp_exact_rate(bx, torch, H, Ob, x_dev, T_dev)
         extra["qp_solves_warm_in_loop"] = qp_solve_rate_warm(bx, torch, H, Ob, x_dev, T_dev, P, adaptive_rho=0)
         extra["small_configs"] = small_configs(bx, torch)
         extra["e2e"] = e2e_rate(bx, torch, H, Ob, st, x0, T_dev, sp)
@@ -601,6 +602,34 @@ def qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev, cone=0, adaptive_rho=0):
             "iters_max": int(it.max().item()), "ms": dt * 1e3,
             "roofline": {"bound": "alu", "achieved": tflops, "peak": peak, "unit": "TFLOP/s", "frac": tflops / peak,
                          "flops_per_qp_iteration": f_it}}
+
+
+def qp_exact_rate(bx, torch, H, Ob, x_dev, T_dev):
+    """The same 49152 QPs solved exactly (qp.solver = EXACT: the float32
+    minimum-norm-point method, one QP per thread); a solve counts when the
+    oracle-call cap (64) did not stop it.  Its Frank-Wolfe gap, an upper bound
+    on Q - Q*, is reported beside it."""
+    G = bx.bodex_fk_contacts(H, Ob, x_dev)["G"]
+    prm = bx.qp_params(max_iter=64, solver=bx.QP_EXACT)
+    bx.bodex_qp_solve_batch(G, T_dev, prm)  # warm-up
+    ts, out = [], None
+    for _ in range(5):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        out = bx.bodex_qp_solve_batch(G, T_dev, prm)
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    dt = float(np.median(ts)) / 1e3
+    ok = (out["status"] & bx.ST_NOT_CONVERGED) == 0
+    it = out["iters"].float()
+    gap = out["res"][..., 1]
+    Q = out["Q"]
+    return {"value": float(ok.sum().item()) / dt, "unit": "exact QP solves/s", "qps": int(ok.numel()),
+            "finished_frac": float(ok.float().mean().item()), "oracle_calls_median": float(it.median().item()),
+            "oracle_calls_max": int(it.max().item()), "ms": dt * 1e3,
+            "gap_within_1e-4Q_plus_1e-6_frac": float((gap <= 1e-4 * Q + 1e-6).float().mean().item())}
 
 
 def qp_iteration_flops(m, cone=0):

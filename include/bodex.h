@@ -187,7 +187,23 @@ typedef struct bodex_qp_params {
                         and not BODEX_ST_NOT_CONVERGED; z, lam, res and iters stay those of
                         the ADMM run.  A QP the exact solve gives up on (200 oracle calls)
                         keeps its ADMM result.  0: off.  bodex_qp_solve_batch only. */
+  int solver;        /* lower-level method.  BODEX_QP_ADMM: the OSQP-form ADMM above.
+                        BODEX_QP_EXACT (pyramid cone, eps_reg = 0): the exact optimum by
+                        Wolfe's minimum-norm-point method in float32, one QP per thread
+                        (the QP is the nearest point of the wrench polytope G C to beta t);
+                        it stops when the Frank-Wolfe gap, an upper bound on Q - Q*, is
+                        <= 1e-5 Q + 1e-7, when float32 offers no further progress (the
+                        oracle's vertex is already in the working set or affinely
+                        dependent on it; the gap bound may then be looser than the
+                        actual error), or after max_iter oracle calls.  Outputs y, Q;
+                        iters = oracle calls; res = (0, the final gap); z = A y clamped
+                        to the row bounds and lam = 0 (the method gives no multipliers);
+                        BODEX_ST_NOT_CONVERGED when the oracle-call cap stopped it.  rho, sigma, alpha, eps_abs, check_every, warm, polish and
+                        adaptive_rho do not apply.  bodex_qp_solve_batch only. */
 } bodex_qp_params;
+
+#define BODEX_QP_ADMM 0
+#define BODEX_QP_EXACT 1
 
 #define BODEX_CONE_PYRAMID 0
 #define BODEX_CONE_ELLIPTIC 1

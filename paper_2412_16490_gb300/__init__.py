@@ -14,7 +14,7 @@ import ctypes as C
 import numpy as np
 
 from . import _binding as _b
-from ._binding import BodexError, CONE_ELLIPTIC, CONE_PYRAMID, ENERGY_DFC, ENERGY_QP, ST_DEGENERATE_NORMAL, ST_NONFINITE, ST_NOT_CONVERGED, ST_POLISHED  # noqa: F401
+from ._binding import BodexError, CONE_ELLIPTIC, CONE_PYRAMID, ENERGY_DFC, ENERGY_QP, ST_DEGENERATE_NORMAL, ST_NONFINITE, ST_NOT_CONVERGED, ST_POLISHED, QP_ADMM, QP_EXACT  # noqa: F401
 
 __all__ = [
     "load", "Hand", "Object", "State", "qp_params", "step_params",
@@ -58,13 +58,15 @@ def _np(a, dt):
 # ---------------------------------------------------------------- parameters
 def qp_params(mu=0.5, beta=1.0, gamma=0.5, rho=0.1, sigma=1e-6, alpha=1.6, eps_abs=0.0, eps_reg=0.0,
               max_iter=50, check_every=10, warm=0, strict=0, cone=0, adaptive_rho=0,
-              polish=0) -> _b.bodex_qp_params:
+              polish=0, solver=0) -> _b.bodex_qp_params:
     """ADMM/QP parameters (struct bodex_qp_params); cone: CONE_PYRAMID or
     CONE_ELLIPTIC; adaptive_rho: residual-balancing rho in solves with a
-    residual target (eps_abs > 0); polish: FP64 solution polishing of
-    converged pyramid QPs in bodex_qp_solve_batch."""
+    residual target (eps_abs > 0); polish: the exact FP64 solve after ADMM
+    in bodex_qp_solve_batch; solver: QP_ADMM or QP_EXACT (the float32
+    minimum-norm-point method; max_iter caps its oracle calls)."""
     return _b.bodex_qp_params(mu, beta, gamma, rho, sigma, alpha, eps_abs, eps_reg, int(max_iter),
-                              int(check_every), int(warm), int(strict), int(cone), int(adaptive_rho), int(polish))
+                              int(check_every), int(warm), int(strict), int(cone), int(adaptive_rho), int(polish),
+                              int(solver))
 
 
 def step_params(params: dict | None = None, qp: _b.bodex_qp_params | None = None,

@@ -25,6 +25,7 @@ ST_NONFINITE = 1
 ST_NOT_CONVERGED = 2
 ST_DEGENERATE_NORMAL = 4
 ST_POLISHED = 8
+QP_ADMM, QP_EXACT = 0, 1
 
 # Every symbol include/bodex.h declares (checked by the CPU test-suite).
 ENERGY_QP, ENERGY_DFC = 0, 1
@@ -56,7 +57,7 @@ class bodex_qp_params(C.Structure):
     _fields_ = [("mu", C.c_float), ("beta", C.c_float), ("gamma", C.c_float), ("rho", C.c_float),
                 ("sigma", C.c_float), ("alpha", C.c_float), ("eps_abs", C.c_float), ("eps_reg", C.c_float),
                 ("max_iter", C.c_int), ("check_every", C.c_int), ("warm", C.c_int), ("strict", C.c_int),
-                ("cone", C.c_int), ("adaptive_rho", C.c_int), ("polish", C.c_int)]
+                ("cone", C.c_int), ("adaptive_rho", C.c_int), ("polish", C.c_int), ("solver", C.c_int)]
 
 
 class bodex_energy_params(C.Structure):

@@ -360,6 +360,10 @@ int check_qp_params(const bodex_qp_params* p, int m) {
     return fail(BODEX_ERR_INVALID, "invalid ADMM parameters");
   if (p->cone != BODEX_CONE_PYRAMID && p->cone != BODEX_CONE_ELLIPTIC)
     return fail(BODEX_ERR_INVALID, "cone must be BODEX_CONE_PYRAMID or BODEX_CONE_ELLIPTIC");
+  if (p->solver != BODEX_QP_ADMM && p->solver != BODEX_QP_EXACT)
+    return fail(BODEX_ERR_INVALID, "solver must be BODEX_QP_ADMM or BODEX_QP_EXACT");
+  if (p->solver == BODEX_QP_EXACT && (p->cone != BODEX_CONE_PYRAMID || p->eps_reg != 0.f || p->max_iter < 1))
+    return fail(BODEX_ERR_INVALID, "the exact solver needs the pyramid cone, eps_reg = 0 and max_iter >= 1");
   return BODEX_OK;
 }
 
@@ -838,6 +842,7 @@ static int fill_args(FusedArgs& A, bodex_hand_t h, bodex_object_t o, const float
                      const bodex_step_params* p) {
   if (!h || !o || !p || !T || s < 1 || s > SMAX || B < 0) return fail(BODEX_ERR_INVALID, "bad arguments");
   if (int r = check_qp_params(&p->qp, h->host.m)) return r;
+  if (p->qp.solver != BODEX_QP_ADMM) return fail(BODEX_ERR_INVALID, "the fused step solves its QPs by ADMM");
   std::memset(&A, 0, sizeof(A));
   A.hand = h->dev;
   A.obj = o->dev;

@@ -78,6 +78,7 @@ struct AdmmCfg {
   int iters, check;
   int fp64_setup;  // build K^-1 in double (set by the host per launch)
   int polish;      // polish converged pyramid QPs (bodex_qp_solve_batch)
+  int solver;      // BODEX_QP_ADMM or BODEX_QP_EXACT
 };
 
 __host__ __device__ inline AdmmCfg admm_cfg(const bodex_qp_params& p) {
@@ -97,6 +98,7 @@ __host__ __device__ inline AdmmCfg admm_cfg(const bodex_qp_params& p) {
   c.check = p.check_every > 0 ? p.check_every : 10;
   c.fp64_setup = 0;
   c.polish = p.polish;
+  c.solver = p.solver;
   return c;
 }
 
@@ -1043,6 +1045,341 @@ struct Wolfe {
       y[a] = s;
     }
     return ok ? calls : -1;
+  }
+};
+
+// ------------------------------------------------------------------ exact QP in float32
+// The same minimum-norm-point method as Wolfe<M, R> (see there), arranged
+// for speed in float32: one QP per thread with every array in registers
+// (loops fully unrolled over the at most 7 points), the nearest point of the
+// affine hull found by a QR factorisation of the differences
+// D = [p_1 - p_0, ...] (modified Gram-Schmidt, each column orthogonalised
+// twice) instead of the normal equations D^T D, whose float32 conditioning
+// (kappa^2) cost accuracy; and vertices held as codes: per contact its best
+// edge k (3 bits) and whether it pushes with f = 1 (1 bit), and the one
+// contact the knapsack fills fractionally with its f.
+// G: the grasp's 6 x 3m matrix (shared memory); b = beta t.  Stops when the
+// Frank-Wolfe gap |x|^2 - x . q_new <= 1e-5 |x|^2 + 1e-7 (an upper bound on
+// Q(y) - Q*); when the oracle returns a vertex already in the set or one
+// affinely dependent on it, or |x|^2 has not fallen by a relative 1e-6 in
+// three steps (float32 has no further progress to offer: the point is the
+// nearest one at float32 resolution, and its gap bound may then be loose);
+// or after max_calls oracle calls.  Returns the calls used,
+// negated when the cap stopped it; gap receives the last Frank-Wolfe gap.
+template <int M>
+struct ExactQP {
+  static constexpr int NV = 3 * M, K = 7;
+  struct Vtx {
+    int code;    // bits 4i..4i+2: contact i's edge k; bit 4i+3: f_i = 1; bits 20..22: fractional contact (7: none)
+    float frac;  // the fractional contact's f
+  };
+  // edge tip directions (1, mu cos(k pi/4), mu sin(k pi/4)): cos, sin of k pi/4
+  __device__ static float ck(int k) {
+    const float h = 0.70710678118654752f;
+    return k == 0 ? 1.f : k == 1 ? h : k == 2 ? 0.f : k == 3 ? -h : k == 4 ? -1.f : k == 5 ? -h : k == 6 ? 0.f : h;
+  }
+  __device__ static float sk(int k) { return ck((k + 6) & 7); }
+  // f_i of contact i in a vertex
+  __device__ static float f_of(const Vtx& v, int i) {
+    if (((v.code >> 20) & 7) == i) return v.frac;
+    return ((v.code >> (4 * i + 3)) & 1) ? 1.f : 0.f;
+  }
+  // linear oracle: the vertex of C minimising x . (G v) (continuous knapsack
+  // over the contacts' best edges), and its point q = G v - b
+  __device__ static Vtx oracle(const float* G, const float* b, const float* x, const AdmmCfg& c, float* q) {
+    float gy[NV];
+#pragma unroll
+    for (int a = 0; a < NV; ++a) {
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < 6; ++r) s = fmaf(G[r * NV + a], x[r], s);
+      gy[a] = s;
+    }
+    float cb[M];
+    int kb[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      float best = gy[3 * i] + c.mu * gy[3 * i + 1];
+      int k0 = 0;
+#pragma unroll
+      for (int k = 1; k < 8; ++k) {
+        const float v = gy[3 * i] + c.mu * fmaf(ck(k), gy[3 * i + 1], sk(k) * gy[3 * i + 2]);
+        if (v < best) best = v, k0 = k;
+      }
+      cb[i] = best;
+      kb[i] = k0;
+    }
+    Vtx v;
+    v.code = 7 << 20;
+    v.frac = 0.f;
+    float sum = 0.f;
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      v.code |= kb[i] << (4 * i);
+      if (cb[i] < 0.f) {
+        v.code |= 1 << (4 * i + 3);
+        sum += 1.f;
+      }
+    }
+    // fill the cheapest contacts not yet at f = 1 until sum f >= gamma
+#pragma unroll 1
+    for (int guard = 0; guard < M && sum < c.gamma; ++guard) {
+      int pick = -1;
+      float pc = 0.f;
+#pragma unroll
+      for (int i = 0; i < M; ++i) {
+        const bool full = (v.code >> (4 * i + 3)) & 1;
+        if (!full && (pick < 0 || cb[i] < pc)) pick = i, pc = cb[i];
+      }
+      if (pick < 0) break;
+      const float add = fminf(1.f, c.gamma - sum);
+      if (add >= 1.f) {
+        v.code |= 1 << (4 * pick + 3);
+      } else {
+        v.code = (v.code & ~(7 << 20)) | (pick << 20);
+        v.frac = add;  // the fractional contact keeps its 'full' bit clear
+      }
+      sum += add;
+      if (add < 1.f) break;
+    }
+    point(G, b, v, c, q);
+    return v;
+  }
+  __device__ static void point(const float* G, const float* b, const Vtx& v, const AdmmCfg& c, float* q) {
+#pragma unroll
+    for (int r = 0; r < 6; ++r) q[r] = -b[r];
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const float f = f_of(v, i);
+      if (f != 0.f) {
+        const int k = (v.code >> (4 * i)) & 7;
+        const float fd = f * c.mu * ck(k), fe = f * c.mu * sk(k);
+#pragma unroll
+        for (int r = 0; r < 6; ++r)
+          q[r] = fmaf(f, G[r * NV + 3 * i], fmaf(fd, G[r * NV + 3 * i + 1], fmaf(fe, G[r * NV + 3 * i + 2], q[r])));
+      }
+    }
+  }
+  __device__ static void accumulate_y(const Vtx& v, float w, const AdmmCfg& c, float* y) {
+#pragma unroll
+    for (int i = 0; i < M; ++i) {
+      const float f = w * f_of(v, i);
+      const int k = (v.code >> (4 * i)) & 7;
+      y[3 * i] += f;
+      y[3 * i + 1] = fmaf(f * c.mu, ck(k), y[3 * i + 1]);
+      y[3 * i + 2] = fmaf(f * c.mu, sk(k), y[3 * i + 2]);
+    }
+  }
+  // nearest point of the affine hull of P[0..n-1]: weights al (sum 1);
+  // false when the differences are (numerically) dependent
+  __device__ static bool affine_min(const float (&P)[K][6], int n, float (&al)[K]) {
+    float U[K - 1][6], R[K - 1][K - 1], sc = 1.f;
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (i < n)
+#pragma unroll
+        for (int r = 0; r < 6; ++r) sc = fmaxf(sc, fabsf(P[i][r]));
+#pragma unroll
+    for (int j = 0; j < K - 1; ++j) {
+      if (j + 1 >= n) break;
+      float u[6];
+#pragma unroll
+      for (int r = 0; r < 6; ++r) u[r] = P[j + 1][r] - P[0][r];
+#pragma unroll
+      for (int i = 0; i < K - 1; ++i) R[i][j] = 0.f;
+#pragma unroll
+      for (int pass = 0; pass < 2; ++pass)
+#pragma unroll
+        for (int i = 0; i < K - 1; ++i) {
+          if (i >= j) break;
+          float d = 0.f;
+#pragma unroll
+          for (int r = 0; r < 6; ++r) d = fmaf(U[i][r], u[r], d);
+          R[i][j] += d;
+#pragma unroll
+          for (int r = 0; r < 6; ++r) u[r] = fmaf(-d, U[i][r], u[r]);
+        }
+      float nn = 0.f;
+#pragma unroll
+      for (int r = 0; r < 6; ++r) nn = fmaf(u[r], u[r], nn);
+      const float rjj = sqrtf(nn);
+      if (!(rjj > 1e-6f * sc)) return false;
+      R[j][j] = rjj;
+      const float inv = 1.f / rjj;
+#pragma unroll
+      for (int r = 0; r < 6; ++r) U[j][r] = u[r] * inv;
+    }
+    // alpha' = -R^-1 U^T p_0, alpha_0 = 1 - sum alpha'
+    float a1[K - 1];
+#pragma unroll
+    for (int j = K - 2; j >= 0; --j) {
+      if (j + 1 >= n) {
+        a1[j] = 0.f;
+        continue;
+      }
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < 6; ++r) s = fmaf(-U[j][r], P[0][r], s);
+#pragma unroll
+      for (int k = K - 2; k > j; --k)
+        if (k + 1 < n) s = fmaf(-R[j][k], a1[k], s);
+      a1[j] = s / R[j][j];
+    }
+    float a0 = 1.f;
+#pragma unroll
+    for (int j = 0; j < K - 1; ++j) {
+      al[j + 1] = a1[j];
+      a0 -= a1[j];
+    }
+    al[0] = a0;
+    return true;
+  }
+
+  __device__ static int solve(const float* G, const float* t, const AdmmCfg& c, int max_calls, float* y, float& Q,
+                              float& gap) {
+    float b[6];
+#pragma unroll
+    for (int r = 0; r < 6; ++r) b[r] = c.beta * t[r];
+    float P[K][6], lam[K], x[6];
+    Vtx V[K];
+    // first vertex: the oracle at y = 0 (x = -b)
+#pragma unroll
+    for (int r = 0; r < 6; ++r) x[r] = -b[r];
+    V[0] = oracle(G, b, x, c, P[0]);
+    int n = 1;
+#pragma unroll
+    for (int i = 0; i < K; ++i) lam[i] = i == 0 ? 1.f : 0.f;
+#pragma unroll
+    for (int r = 0; r < 6; ++r) x[r] = P[0][r];
+    int calls = 1, stall = 0;
+    bool capped = false;
+    float prev_xx = 3.4e38f;
+    gap = 0.f;
+#pragma unroll 1
+    for (;;) {
+      float q[6];
+      const Vtx vn = oracle(G, b, x, c, q);
+      ++calls;
+      float xx = 0.f, xq = 0.f;
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        xx = fmaf(x[r], x[r], xx);
+        xq = fmaf(x[r], q[r], xq);
+      }
+      gap = xx - xq;
+      if (gap <= 1e-5f * xx + 1e-7f || n >= K) break;
+      // |x| falls at every major step in exact arithmetic; three steps
+      // without a relative 1e-6 decrease: float32 resolution is reached
+      stall = xx > prev_xx * (1.f - 1e-6f) ? stall + 1 : 0;
+      prev_xx = xx;
+      if (stall >= 3) break;
+      bool seen = false;  // the oracle cycles back to a vertex of the set
+#pragma unroll
+      for (int i = 0; i < K; ++i)
+        if (i < n) seen = seen || (V[i].code == vn.code && V[i].frac == vn.frac);
+      if (seen) break;
+      if (calls >= max_calls) {
+        capped = true;
+        break;
+      }
+      // add the vertex with weight 0 (slot n), then minor cycles
+#pragma unroll
+      for (int i = 0; i < K; ++i)
+        if (i == n) {
+          V[i] = vn;
+#pragma unroll
+          for (int r = 0; r < 6; ++r) P[i][r] = q[r];
+          lam[i] = 0.f;
+        }
+      ++n;
+      bool stop = false;
+#pragma unroll 1
+      for (int guard = 0; guard < 2 * K; ++guard) {
+        float al[K];
+        if (!affine_min(P, n, al)) {  // dependent points: drop the last one, keep the current weights
+          --n;
+          float tot = 0.f;
+#pragma unroll
+          for (int i = 0; i < K; ++i) tot += i < n ? lam[i] : 0.f;
+          const float it = tot > 0.f ? 1.f / tot : 0.f;
+#pragma unroll
+          for (int i = 0; i < K; ++i) lam[i] = i < n ? (tot > 0.f ? lam[i] * it : (i == 0 ? 1.f : 0.f)) : 0.f;
+          stop = true;
+          break;
+        }
+        bool inside = true;
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+          if (i < n) inside = inside && al[i] > 0.f;
+        if (inside) {
+#pragma unroll
+          for (int i = 0; i < K; ++i) lam[i] = i < n ? al[i] : 0.f;
+          break;
+        }
+        // step towards al until the first weight reaches zero; drop that point
+        float th = 1.f;
+        int drop = -1;
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+          if (i < n && al[i] <= 0.f) {
+            const float den = lam[i] - al[i];
+            const float ti = den > 0.f ? lam[i] / den : 0.f;
+            if (drop < 0 || ti < th) th = ti, drop = i;
+          }
+        float tot = 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+          if (i < n) {
+            lam[i] = i == drop ? 0.f : fmaxf(fmaf(th, al[i] - lam[i], lam[i]), 0.f);
+            tot += lam[i];
+          }
+        // compact: move the last point into the dropped slot
+        const int last = n - 1;
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+          if (i == drop && drop != last) {
+#pragma unroll
+            for (int j = 0; j < K; ++j)
+              if (j == last) {
+                V[i] = V[j];
+                lam[i] = lam[j];
+#pragma unroll
+                for (int r = 0; r < 6; ++r) P[i][r] = P[j][r];
+              }
+          }
+        --n;
+        const float it = tot > 0.f ? 1.f / tot : 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i) lam[i] = i < n ? lam[i] * it : 0.f;
+        if (n == 1) {
+          lam[0] = 1.f;
+          break;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+          if (i < n) s = fmaf(lam[i], P[i][r], s);
+        x[r] = s;
+      }
+      if (stop) break;
+    }
+#pragma unroll
+    for (int a = 0; a < NV; ++a) y[a] = 0.f;
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+      if (i < n) accumulate_y(V[i], lam[i], c, y);
+    Q = 0.f;
+#pragma unroll
+    for (int r = 0; r < 6; ++r) {
+      float s = c.beta * t[r];
+#pragma unroll
+      for (int a = 0; a < NV; ++a) s = fmaf(-G[r * NV + a], y[a], s);
+      Q = fmaf(s, s, Q);
+    }
+    return capped ? -calls : calls;
   }
 };
 

@@ -564,6 +564,63 @@ __global__ void __launch_bounds__(CTA_LANES, 4) qp_solve_kernel(const float* __r
   }
 }
 
+// ============================================================================ kernel: exact QPs (qp.solver = EXACT)
+// One thread per QP, the minimum-norm-point solve in float32 (ExactQP); the
+// block's grasps' G staged in shared memory.  Outputs: y, Q, the oracle
+// calls in iters, res = (0, the final Frank-Wolfe gap, an upper bound on
+// Q - Q*), z = A y clamped to the row bounds, lam = 0 (the method gives no
+// multipliers); BODEX_ST_NOT_CONVERGED when the oracle-call cap stopped it.
+template <int M>
+__global__ void __launch_bounds__(128) qp_exact_kernel(const float* __restrict__ Gin, int B,
+                                                       const float* __restrict__ T, int S, AdmmCfg cfg, float* y_out,
+                                                       float* z_out, float* l_out, float* Qout, int32_t* iters_out,
+                                                       int32_t* status_out, float* res_out) {
+  constexpr int NV = 3 * M, NC = 9 * M + 1;
+  extern __shared__ __align__(16) float smem[];
+  const int GPB = blockDim.x / S;
+  const size_t g0 = (size_t)blockIdx.x * GPB;
+  const int ng = (int)min((size_t)GPB, (size_t)B - g0);
+  for (int e = threadIdx.x; e < ng * 6 * NV; e += blockDim.x) smem[e] = Gin[g0 * 6 * NV + e];
+  __syncthreads();
+  const int gl = threadIdx.x / S, j = threadIdx.x % S;
+  if (gl >= ng) return;
+  const size_t q = (g0 + gl) * S + j;
+  const float* G = smem + gl * 6 * NV;
+  float t[6], y[NV], Q, gap;
+#pragma unroll
+  for (int r = 0; r < 6; ++r) t[r] = T[j * 6 + r];
+  const int ret = ExactQP<M>::solve(G, t, cfg, cfg.iters, y, Q, gap);
+  const int calls = ret < 0 ? -ret : ret;
+  bool fin = isfinite(Q);
+#pragma unroll
+  for (int a = 0; a < NV; ++a) {
+    y_out[q * NV + a] = y[a];
+    fin = fin && isfinite(y[a]);
+  }
+  float sumn = 0.f;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    const float yn = y[3 * i], yd = y[3 * i + 1], ye = y[3 * i + 2];
+    sumn += yn;
+    z_out[q * NC + 9 * i] = fminf(fmaxf(yn, 0.f), 1.f);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      z_out[q * NC + 9 * i + 1 + k] = fminf(fmaf(kFC[k], yd, fmaf(kFS[k], ye, -cfg.mu_c8 * yn)), 0.f);
+  }
+  z_out[q * NC + 9 * M] = fmaxf(sumn, cfg.gamma);
+  for (int r = 0; r < NC; ++r) l_out[q * NC + r] = 0.f;
+  Qout[q] = Q;
+  if (iters_out) iters_out[q] = calls;
+  if (res_out) {
+    res_out[2 * q] = 0.f;
+    res_out[2 * q + 1] = gap;
+  }
+  int st = 0;
+  if (!fin) st |= BODEX_ST_NONFINITE;
+  if (ret < 0) st |= BODEX_ST_NOT_CONVERGED;
+  if (status_out) status_out[q] = st;
+}
+
 // ============================================================================ kernel: solution polishing
 // A pass after qp_solve_kernel when qp.polish is set (pyramid QPs with
 // eps_reg = 0): one thread per QP solves the QP exactly in FP64 by the
@@ -1108,6 +1165,13 @@ template <int M>
 inline int run_qp(const float* G, int B, const float* T, int s, const AdmmCfg& cfg, int warm, float* y, float* z,
            float* lam, float* Q, int32_t* iters, int32_t* status, float* res, cudaStream_t st) {
   if (B == 0) return BODEX_OK;
+  if (cfg.solver == BODEX_QP_EXACT) {
+    const int gpb = std::max(1, 128 / s);
+    const size_t bytes = 4u * (size_t)gpb * 6 * 3 * M;
+    qp_exact_kernel<M><<<(B + gpb - 1) / gpb, gpb * s, bytes, st>>>(G, B, T, s, cfg, y, z, lam, Q, iters, status,
+                                                                    res);
+    return launch_err("qp_exact_kernel launch");
+  }
   const int gpb = cfg.cone ? qp_gpb<M, CONE_SOC>(s) : qp_gpb<M, CONE_PYR>(s);
   const size_t bytes = cfg.cone ? LayQP<M, CONE_SOC>::bytes(gpb, s) : LayQP<M, CONE_PYR>::bytes(gpb, s);
   if (cfg.cone) {

@@ -84,6 +84,24 @@ def test_fullsize_qp_batch_sampled(full):
     assert (d >= lo - tol).all() and (d <= hi + tol).all()
 
 
+def test_fullsize_qp_batch_exact_solver(full):
+    """The same 49,152 QPs with qp.solver = EXACT: no QP stopped by the cap,
+    and the sampled grasps' values within 1e-4 |Q*| + 1e-6 of the oracle's."""
+    hand, obj, x0, T, P, H, Ob = full
+    G = bx.bodex_fk_contacts(H, Ob, cuda(x0))["G"]
+    out = bx.bodex_qp_solve_batch(G, cuda(T), bx.qp_params(mu=MU, beta=BETA, gamma=GAMMA, max_iter=64,
+                                                            solver=bx.QP_EXACT))
+    st = host(out["status"])
+    assert (st == 0).all()
+    Gs = host(G)[SAMPLE].astype(np.float64)
+    ref = O.qp_solve(Gs, T, mu=MU, beta=BETA, gamma=GAMMA)
+    y = host(out["y"])[SAMPLE].astype(np.float64)
+    Qy = ((BETA * T[None].astype(np.float64) - np.einsum("bri,bsi->bsr", Gs, y)) ** 2).sum(-1)
+    bar = 1e-4 * np.abs(ref["Q"]) + 1e-6
+    assert (np.abs(Qy - ref["Q"]) <= bar).all()
+    assert (np.abs(host(out["Q"])[SAMPLE] - ref["Q"]) <= bar).all()
+
+
 def test_fullsize_energy_gradient_sampled(full):
     hand, obj, x0, T, P, H, Ob = full
     Pr = dict(P, eps_reg=1e-3)

@@ -148,6 +148,43 @@ def test_qp_value_north_star_bar(wl, B, request):
     assert (Ay[..., :9 * m][..., facet] <= 1e-6).all()
 
 
+@pytest.mark.parametrize("wl,B", [("tiny", 64), ("paper_small", 96), ("paper_near", 64)])
+def test_qp_exact_solver_north_star_bar(wl, B, request):
+    """qp.solver = EXACT (the float32 minimum-norm-point method, no ADMM):
+    no QP stopped by the oracle-call cap; every QP's value within
+    1e-4 |Q*| + 1e-6 of the oracle's; the Frank-Wolfe gap reported in
+    res[..., 1] a valid upper bound on Q - Q* (to float32 rounding, 1e-6);
+    forces feasible to 1e-6."""
+    hand, obj, x0, T, P = request.getfixturevalue(wl)
+    G32 = _oracle_G(hand, obj, x0[:B], T, P)
+    G = G32.astype(np.float64)
+    ref = O.qp_solve(G, T, mu=MU, beta=BETA, gamma=GAMMA)
+    assert (ref["status"] == 0).all()
+    prm = bx.qp_params(mu=MU, beta=BETA, gamma=GAMMA, max_iter=64, solver=bx.QP_EXACT)
+    out = bx.bodex_qp_solve_batch(cuda(G32), cuda(T), prm)
+    st = host(out["status"])
+    assert (st == 0).all()
+    y = host(out["y"]).astype(np.float64)
+    Qy = ((BETA * T[None].astype(np.float64) - np.einsum("bri,bsi->bsr", G, y)) ** 2).sum(-1)
+    bar = qp_bar(ref["Q"])
+    assert (np.abs(host(out["Q"]) - ref["Q"]) <= bar).all()
+    assert (np.abs(Qy - ref["Q"]) <= bar).all()
+    gap = host(out["res"])[..., 1].astype(np.float64)
+    assert (Qy - ref["Q"] <= gap + 1e-6).all()
+    assert (host(out["iters"]) <= 64).all()
+    m = G.shape[-1] // 3
+    Ay = np.einsum("ci,bsi->bsc", admm_rows(m, MU), y)
+    assert (Ay[..., 9 * m] >= GAMMA - 1e-6).all()
+    assert (Ay[..., 0:9 * m:9] >= -1e-6).all() and (Ay[..., 0:9 * m:9] <= 1 + 1e-6).all()
+    facet = np.ones(9 * m, bool)
+    facet[0::9] = False
+    assert (Ay[..., :9 * m][..., facet] <= 1e-6).all()
+    # z is A y clamped to the bounds, lam is zero
+    np.testing.assert_allclose(host(out["z"])[..., :9 * m][..., facet], np.minimum(Ay[..., :9 * m][..., facet], 0),
+                               atol=1e-6)
+    assert (host(out["lam"]) == 0).all()
+
+
 @pytest.mark.parametrize("wl,B", [("tiny", 64), ("paper_small", 37), ("paper_near", 64)])
 def test_qp_value_within_certificate(wl, B, request):
     """ADMM alone (no polishing) at a 1e-6 residual: every QP converges and
@@ -247,6 +284,13 @@ def test_qp_warm_start_and_edge_cases():
     # fixed iteration count (eps_abs = 0) runs exactly max_iter iterations
     fixed = bx.bodex_qp_solve_batch(cuda(G32), cuda(T), bx.qp_params(max_iter=37))
     assert (host(fixed["iters"]) == 37).all()
+    # the exact solver: empty batch, and the shapes it refuses
+    e = bx.bodex_qp_solve_batch(cuda(G32[:0]), cuda(T), bx.qp_params(solver=bx.QP_EXACT))
+    assert e["Q"].numel() == 0
+    for bad in (dict(eps_reg=1e-3), dict(cone=bx.CONE_ELLIPTIC), dict(max_iter=0)):
+        with pytest.raises(bx.BodexError) as ei:
+            bx.bodex_qp_solve_batch(cuda(G32), cuda(T), bx.qp_params(solver=bx.QP_EXACT, **bad))
+        assert ei.value.code == 1
 
 
 # ------------------------------------------------------------------ energy and gradient

@@ -842,7 +842,6 @@ static int fill_args(FusedArgs& A, bodex_hand_t h, bodex_object_t o, const float
                      const bodex_step_params* p) {
   if (!h || !o || !p || !T || s < 1 || s > SMAX || B < 0) return fail(BODEX_ERR_INVALID, "bad arguments");
   if (int r = check_qp_params(&p->qp, h->host.m)) return r;
-  if (p->qp.solver != BODEX_QP_ADMM) return fail(BODEX_ERR_INVALID, "the fused step solves its QPs by ADMM");
   std::memset(&A, 0, sizeof(A));
   A.hand = h->dev;
   A.obj = o->dev;
@@ -986,8 +985,9 @@ int bodex_step_multi(const bodex_job* jobs, int n_jobs, const bodex_step_params*
   MA->cta_begin[nj] = total;
   int r = BODEX_OK;
   if (nj > 0) {
-    const bool adapt = params->qp.eps_abs > 0.f && params->qp.adaptive_rho;
-    r = launch_multi(adapt, *MA, total, bytes, as_stream(stream));
+    const bool exact = params->qp.solver == BODEX_QP_EXACT;
+    const bool adapt = !exact && params->qp.eps_abs > 0.f && params->qp.adaptive_rho;
+    r = launch_multi(adapt, exact, *MA, total, bytes, as_stream(stream));
     if (r == BODEX_OK)
       for (int k = 0; k < nj; ++k) jobs[take[k]].state->t += jobs[take[k]].n_steps;
   }

@@ -1235,28 +1235,133 @@ struct ExactQP {
     return true;
   }
 
-  __device__ static int solve(const float* G, const float* t, const AdmmCfg& c, int max_calls, float* y, float& Q,
-                              float& gap) {
+  // The working set ("corral"): n points with their vertex codes and weights.
+  struct Corral {
+    int n;
+    Vtx V[K];
+    float lam[K];
+  };
+  // Minor cycles of Wolfe's method on (P, C): the nearest point of the
+  // affine hull of the set; while it leaves the simplex, step towards it
+  // until a weight reaches 0 and drop that point.  Returns false when the
+  // points turned out dependent (the last one is dropped, the weights kept).
+  __device__ static bool minor(float (&P)[K][6], Corral& C) {
+    int& n = C.n;
+#pragma unroll 1
+    for (int guard = 0; guard < 2 * K; ++guard) {
+      float al[K];
+      if (!affine_min(P, n, al)) {  // dependent points: drop the last one, keep the current weights
+        --n;
+        float tot = 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i) tot += i < n ? C.lam[i] : 0.f;
+        const float it = tot > 0.f ? 1.f / tot : 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i) C.lam[i] = i < n ? (tot > 0.f ? C.lam[i] * it : (i == 0 ? 1.f : 0.f)) : 0.f;
+        return false;
+      }
+      bool inside = true;
+#pragma unroll
+      for (int i = 0; i < K; ++i)
+        if (i < n) inside = inside && al[i] > 0.f;
+      if (inside) {
+#pragma unroll
+        for (int i = 0; i < K; ++i) C.lam[i] = i < n ? al[i] : 0.f;
+        return true;
+      }
+      float th = 1.f;
+      int drop = -1;
+#pragma unroll
+      for (int i = 0; i < K; ++i)
+        if (i < n && al[i] <= 0.f) {
+          const float den = C.lam[i] - al[i];
+          const float ti = den > 0.f ? C.lam[i] / den : 0.f;
+          if (drop < 0 || ti < th) th = ti, drop = i;
+        }
+      float tot = 0.f;
+#pragma unroll
+      for (int i = 0; i < K; ++i)
+        if (i < n) {
+          C.lam[i] = i == drop ? 0.f : fmaxf(fmaf(th, al[i] - C.lam[i], C.lam[i]), 0.f);
+          tot += C.lam[i];
+        }
+      // compact: move the last point into the dropped slot
+      const int last = n - 1;
+#pragma unroll
+      for (int i = 0; i < K; ++i)
+        if (i == drop && drop != last) {
+#pragma unroll
+          for (int j = 0; j < K; ++j)
+            if (j == last) {
+              C.V[i] = C.V[j];
+              C.lam[i] = C.lam[j];
+#pragma unroll
+              for (int r = 0; r < 6; ++r) P[i][r] = P[j][r];
+            }
+        }
+      --n;
+      const float it = tot > 0.f ? 1.f / tot : 0.f;
+#pragma unroll
+      for (int i = 0; i < K; ++i) C.lam[i] = i < n ? C.lam[i] * it : 0.f;
+      if (n == 1) {
+        C.lam[0] = 1.f;
+        return true;
+      }
+    }
+    return true;
+  }
+
+  // Solves the QP starting from the corral C (C.n == 0: a cold start at the
+  // oracle's vertex for y = 0); C receives the final corral, which a later
+  // solve of a nearby QP (the next upper step's G) can start from: its
+  // points are recomputed for the new G and the minor cycles make it a valid
+  // corral again before the first oracle call.
+  __device__ static int solve(const float* G, const float* t, const AdmmCfg& c, int max_calls, Corral& C, float* y,
+                              float& Q, float& gap) {
     float b[6];
 #pragma unroll
     for (int r = 0; r < 6; ++r) b[r] = c.beta * t[r];
-    float P[K][6], lam[K], x[6];
-    Vtx V[K];
-    // first vertex: the oracle at y = 0 (x = -b)
+    float P[K][6], x[6];
+    int calls = 0;
+    if (C.n <= 0 || C.n > K) {  // cold: the oracle's vertex at y = 0 (x = -b)
 #pragma unroll
-    for (int r = 0; r < 6; ++r) x[r] = -b[r];
-    V[0] = oracle(G, b, x, c, P[0]);
-    int n = 1;
+      for (int r = 0; r < 6; ++r) x[r] = -b[r];
+      C.V[0] = oracle(G, b, x, c, P[0]);
+      C.n = 1;
+      ++calls;
 #pragma unroll
-    for (int i = 0; i < K; ++i) lam[i] = i == 0 ? 1.f : 0.f;
+      for (int i = 0; i < K; ++i) C.lam[i] = i == 0 ? 1.f : 0.f;
+    } else {  // warm: the stored vertices' points for this G
+      float tot = 0.f;
 #pragma unroll
-    for (int r = 0; r < 6; ++r) x[r] = P[0][r];
-    int calls = 1, stall = 0;
+      for (int i = 0; i < K; ++i)
+        if (i < C.n) {
+          point(G, b, C.V[i], c, P[i]);
+          C.lam[i] = fmaxf(C.lam[i], 0.f);
+          tot += C.lam[i];
+        } else {
+          C.lam[i] = 0.f;
+        }
+      const float it = tot > 0.f ? 1.f / tot : 0.f;
+#pragma unroll
+      for (int i = 0; i < K; ++i) C.lam[i] = i < C.n ? (tot > 0.f ? C.lam[i] * it : 1.f / C.n) : 0.f;
+      if (C.n > 1) minor(P, C);
+    }
+    int& n = C.n;
     bool capped = false;
+    int stall = 0;
     float prev_xx = 3.4e38f;
     gap = 0.f;
 #pragma unroll 1
     for (;;) {
+#pragma unroll
+      for (int r = 0; r < 6; ++r) {
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+          if (i < n) s = fmaf(C.lam[i], P[i][r], s);
+        x[r] = s;
+      }
       float q[6];
       const Vtx vn = oracle(G, b, x, c, q);
       ++calls;
@@ -1276,7 +1381,7 @@ struct ExactQP {
       bool seen = false;  // the oracle cycles back to a vertex of the set
 #pragma unroll
       for (int i = 0; i < K; ++i)
-        if (i < n) seen = seen || (V[i].code == vn.code && V[i].frac == vn.frac);
+        if (i < n) seen = seen || (C.V[i].code == vn.code && C.V[i].frac == vn.frac);
       if (seen) break;
       if (calls >= max_calls) {
         capped = true;
@@ -1286,91 +1391,29 @@ struct ExactQP {
 #pragma unroll
       for (int i = 0; i < K; ++i)
         if (i == n) {
-          V[i] = vn;
+          C.V[i] = vn;
 #pragma unroll
           for (int r = 0; r < 6; ++r) P[i][r] = q[r];
-          lam[i] = 0.f;
+          C.lam[i] = 0.f;
         }
       ++n;
-      bool stop = false;
-#pragma unroll 1
-      for (int guard = 0; guard < 2 * K; ++guard) {
-        float al[K];
-        if (!affine_min(P, n, al)) {  // dependent points: drop the last one, keep the current weights
-          --n;
-          float tot = 0.f;
+      if (!minor(P, C)) {  // the newcomer is dependent: the current point stands
 #pragma unroll
-          for (int i = 0; i < K; ++i) tot += i < n ? lam[i] : 0.f;
-          const float it = tot > 0.f ? 1.f / tot : 0.f;
+        for (int r = 0; r < 6; ++r) {
+          float s = 0.f;
 #pragma unroll
-          for (int i = 0; i < K; ++i) lam[i] = i < n ? (tot > 0.f ? lam[i] * it : (i == 0 ? 1.f : 0.f)) : 0.f;
-          stop = true;
-          break;
+          for (int i = 0; i < K; ++i)
+            if (i < n) s = fmaf(C.lam[i], P[i][r], s);
+          x[r] = s;
         }
-        bool inside = true;
-#pragma unroll
-        for (int i = 0; i < K; ++i)
-          if (i < n) inside = inside && al[i] > 0.f;
-        if (inside) {
-#pragma unroll
-          for (int i = 0; i < K; ++i) lam[i] = i < n ? al[i] : 0.f;
-          break;
-        }
-        // step towards al until the first weight reaches zero; drop that point
-        float th = 1.f;
-        int drop = -1;
-#pragma unroll
-        for (int i = 0; i < K; ++i)
-          if (i < n && al[i] <= 0.f) {
-            const float den = lam[i] - al[i];
-            const float ti = den > 0.f ? lam[i] / den : 0.f;
-            if (drop < 0 || ti < th) th = ti, drop = i;
-          }
-        float tot = 0.f;
-#pragma unroll
-        for (int i = 0; i < K; ++i)
-          if (i < n) {
-            lam[i] = i == drop ? 0.f : fmaxf(fmaf(th, al[i] - lam[i], lam[i]), 0.f);
-            tot += lam[i];
-          }
-        // compact: move the last point into the dropped slot
-        const int last = n - 1;
-#pragma unroll
-        for (int i = 0; i < K; ++i)
-          if (i == drop && drop != last) {
-#pragma unroll
-            for (int j = 0; j < K; ++j)
-              if (j == last) {
-                V[i] = V[j];
-                lam[i] = lam[j];
-#pragma unroll
-                for (int r = 0; r < 6; ++r) P[i][r] = P[j][r];
-              }
-          }
-        --n;
-        const float it = tot > 0.f ? 1.f / tot : 0.f;
-#pragma unroll
-        for (int i = 0; i < K; ++i) lam[i] = i < n ? lam[i] * it : 0.f;
-        if (n == 1) {
-          lam[0] = 1.f;
-          break;
-        }
+        break;
       }
-#pragma unroll
-      for (int r = 0; r < 6; ++r) {
-        float s = 0.f;
-#pragma unroll
-        for (int i = 0; i < K; ++i)
-          if (i < n) s = fmaf(lam[i], P[i][r], s);
-        x[r] = s;
-      }
-      if (stop) break;
     }
 #pragma unroll
     for (int a = 0; a < NV; ++a) y[a] = 0.f;
 #pragma unroll
     for (int i = 0; i < K; ++i)
-      if (i < n) accumulate_y(V[i], lam[i], c, y);
+      if (i < n) accumulate_y(C.V[i], C.lam[i], c, y);
     Q = 0.f;
 #pragma unroll
     for (int r = 0; r < 6; ++r) {

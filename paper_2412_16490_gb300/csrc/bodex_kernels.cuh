@@ -589,7 +589,9 @@ __global__ void __launch_bounds__(128) qp_exact_kernel(const float* __restrict__
   float t[6], y[NV], Q, gap;
 #pragma unroll
   for (int r = 0; r < 6; ++r) t[r] = T[j * 6 + r];
-  const int ret = ExactQP<M>::solve(G, t, cfg, cfg.iters, y, Q, gap);
+  typename ExactQP<M>::Corral C;
+  C.n = 0;
+  const int ret = ExactQP<M>::solve(G, t, cfg, cfg.iters, C, y, Q, gap);
   const int calls = ret < 0 ? -ret : ret;
   bool fin = isfinite(Q);
 #pragma unroll
@@ -693,8 +695,14 @@ enum { MODE_EVAL = 0, MODE_STEP = 1, MODE_ADJOINT = 2 };
 // CONE_ANY reads it from the arguments (the several-job kernel).  ADAPT:
 // whether the kernel contains the adaptive-rho solve (residual-target
 // solves); kernels for fixed iteration counts leave it out, as its code
-// costs the fixed loop registers.
+// costs the fixed loop registers.  CONE_EXACT: the pyramid's QPs solved
+// exactly (qp.solver = EXACT, ExactQP) instead of by ADMM: no K^-1 set-up;
+// each QP's working set (corral) carries over to the next upper step in
+// the state's warm-start array: word 0 the point count, then 7 vertex
+// codes, 7 fractional forces and 7 weights (component-major, like the ADMM
+// iterate it replaces).
 constexpr int CONE_ANY = -1;
+constexpr int CONE_EXACT = 2;
 
 template <int M, int MODE, int CONE = CONE_ANY, bool ADAPT = false>
 __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, float* smem) {
@@ -743,7 +751,7 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
     for (int a = 0; a < NV; ++a) y[a] = A.yin[q * NV + a];
 #pragma unroll
     for (int r = 0; r < NC; ++r) w[r] = 0.f;
-  } else if (MODE == MODE_EVAL && active && A.qy) {
+  } else if (MODE == MODE_EVAL && active && A.qy && CONE != CONE_EXACT) {
 #pragma unroll
     for (int a = 0; a < NV; ++a) y[a] = A.qy[a * NQ + q];
 #pragma unroll
@@ -780,7 +788,7 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
                       per + L::oRY + 3 * A.cd.K, per + L::oRY + 3 * A.cd.K + 6 * (H.n + 1), per + L::oGC,
                       per + L::oGC + MAXD);
     // ---- A4: K^-1 per grasp (at the grasp's current penalty)
-    if (MODE != MODE_ADJOINT && !A.dfc) {
+    if (MODE != MODE_ADJOINT && !A.dfc && CONE != CONE_EXACT) {
       if constexpr (ADAPT) {
         AdmmCfg cg = cfg;
         cg.rho = sc[3];
@@ -810,7 +818,7 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
         Q = fmaf(cfg.eps_reg * y[a], y[a], Q);  // regularised value when eps_reg > 0
       }
       per[L::oQ + lane] = Q;
-      if (MODE == MODE_STEP) {
+      if (MODE == MODE_STEP && CONE != CONE_EXACT) {
 #pragma unroll
         for (int a = 0; a < NV; ++a) A.qy[a * NQ + q] = y[a];
 #pragma unroll
@@ -822,7 +830,37 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
       if (st) atomicOr(stat, st);
     };
     const bool soc = CONE == CONE_ANY ? cfg.cone != 0 : CONE == CONE_SOC;
-    if constexpr (ADAPT) {
+    if constexpr (CONE == CONE_EXACT) {
+      // the exact lower level: each lane solves its QP from the corral its
+      // previous step left (cold at the first step of a run)
+      if (active && !A.dfc && MODE != MODE_ADJOINT) {
+        typename ExactQP<M>::Corral C;
+        C.n = 0;
+        if (A.qw) {
+          C.n = __float_as_int(A.qw[q]);
+#pragma unroll
+          for (int i = 0; i < ExactQP<M>::K; ++i) {
+            C.V[i].code = __float_as_int(A.qw[(1 + i) * NQ + q]);
+            C.V[i].frac = A.qw[(8 + i) * NQ + q];
+            C.lam[i] = A.qw[(15 + i) * NQ + q];
+          }
+        }
+        float Qx, gap;
+        const int ret = ExactQP<M>::solve(Gs, t, cfg, cfg.iters, C, y, Qx, gap);
+        if (A.qw) {
+          A.qw[q] = __int_as_float(C.n);
+#pragma unroll
+          for (int i = 0; i < ExactQP<M>::K; ++i) {
+            A.qw[(1 + i) * NQ + q] = __int_as_float(C.V[i].code);
+            A.qw[(8 + i) * NQ + q] = C.V[i].frac;
+            A.qw[(15 + i) * NQ + q] = C.lam[i];
+          }
+        }
+        if (step == A.n_steps - 1) atomicMax(reinterpret_cast<int*>(sc + 2), __float_as_int(fmaxf(gap, 0.f)));
+        if (ret < 0) atomicOr(stat, BODEX_ST_NOT_CONVERGED);
+      }
+      if (active && !A.dfc) finish_qp();
+    } else if constexpr (ADAPT) {
       // solves with a residual target adapt rho per grasp (every thread takes
       // part); the iterate is stored with rho0 = cfg.rho and re-expressed at
       // the grasp's rho here
@@ -1025,7 +1063,7 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
       A.av[(size_t)b * D + k] = avs[k];
     }
   }
-  if (MODE == MODE_EVAL && A.qy) {
+  if (MODE == MODE_EVAL && A.qy && CONE != CONE_EXACT) {
 #pragma unroll
     for (int a = 0; a < NV; ++a) A.qy[a * NQ + q] = y[a];
 #pragma unroll
@@ -1040,7 +1078,7 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
 }
 
 template <int M, int MODE, int CONE, bool ADAPT>
-__global__ void __launch_bounds__(CTA_LANES, 4) fused_kernel(FusedArgs A) {
+__global__ void __launch_bounds__(CTA_LANES, CONE == CONE_EXACT ? 2 : 4) fused_kernel(FusedArgs A) {
   extern __shared__ __align__(16) float smem[];
   fused_cta<M, MODE, CONE, ADAPT>(A, blockIdx.x, A.gpb, smem);
 }
@@ -1060,18 +1098,19 @@ struct MultiArgs {
 
 static_assert(sizeof(MultiArgs) <= 32000, "job table must fit in the kernel parameter space");
 
-template <bool ADAPT>
-__global__ void __launch_bounds__(CTA_LANES, 4) multi_kernel(const __grid_constant__ MultiArgs A) {
+template <bool ADAPT, bool EXACT = false>
+__global__ void __launch_bounds__(CTA_LANES, EXACT ? 2 : 4) multi_kernel(const __grid_constant__ MultiArgs A) {
   extern __shared__ __align__(16) float smem[];
+  constexpr int CN = EXACT ? CONE_EXACT : CONE_ANY;
   const int c = blockIdx.x;
   int j = 0;
   while (j + 1 < A.n_jobs && c >= A.cta_begin[j + 1]) ++j;
   const FusedArgs& J = A.job[j];
   const int cta = c - A.cta_begin[j];
   switch (A.m[j]) {
-    case 3: fused_cta<3, MODE_STEP, CONE_ANY, ADAPT>(J, cta, J.gpb, smem); break;
-    case 4: fused_cta<4, MODE_STEP, CONE_ANY, ADAPT>(J, cta, J.gpb, smem); break;
-    default: fused_cta<5, MODE_STEP, CONE_ANY, ADAPT>(J, cta, J.gpb, smem); break;
+    case 3: fused_cta<3, MODE_STEP, CN, ADAPT>(J, cta, J.gpb, smem); break;
+    case 4: fused_cta<4, MODE_STEP, CN, ADAPT>(J, cta, J.gpb, smem); break;
+    default: fused_cta<5, MODE_STEP, CN, ADAPT>(J, cta, J.gpb, smem); break;
   }
 }
 
@@ -1151,6 +1190,8 @@ inline int run_fused(int mode, const FusedArgs& A0, cudaStream_t st) {
   };
   int r;
   if (mode == MODE_ADJOINT) r = go(fused_kernel<M, MODE_ADJOINT, CONE_PYR, false>);  // no lower-level solve
+  else if (A.cfg.solver == BODEX_QP_EXACT)
+    r = mode == MODE_STEP ? go(fused_kernel<M, MODE_STEP, CONE_EXACT, false>) : go(fused_kernel<M, MODE_EVAL, CONE_EXACT, false>);
   else if (mode == MODE_STEP)
     r = soc ? (adapt ? go(fused_kernel<M, MODE_STEP, CONE_SOC, true>) : go(fused_kernel<M, MODE_STEP, CONE_SOC, false>))
             : (adapt ? go(fused_kernel<M, MODE_STEP, CONE_PYR, true>) : go(fused_kernel<M, MODE_STEP, CONE_PYR, false>));
@@ -1199,4 +1240,4 @@ int launch_fused_m4(int mode, const FusedArgs& A, cudaStream_t st);
 int launch_fused_m5(int mode, const FusedArgs& A, cudaStream_t st);
 int launch_qp(int m, const float* G, int B, const float* T, int s, const AdmmCfg& cfg, int warm, float* y, float* z,
               float* lam, float* Q, int32_t* iters, int32_t* status, float* res, cudaStream_t st);
-int launch_multi(bool adapt, const MultiArgs& MA, int total, size_t bytes, cudaStream_t st);
+int launch_multi(bool adapt, bool exact, const MultiArgs& MA, int total, size_t bytes, cudaStream_t st);

@@ -1,10 +1,12 @@
 // The several-job step kernel (bodex_kernels.cuh).
 #include "bodex_kernels.cuh"
 
-int launch_multi(bool adapt, const MultiArgs& MA, int total, size_t bytes, cudaStream_t st) {
-  int r = adapt ? ensure_smem(multi_kernel<true>, bytes) : ensure_smem(multi_kernel<false>, bytes);
-  if (r != BODEX_OK) return r;
-  if (adapt) multi_kernel<true><<<total, CTA_LANES, bytes, st>>>(MA);
-  else multi_kernel<false><<<total, CTA_LANES, bytes, st>>>(MA);
-  return launch_err("multi_kernel launch");
+int launch_multi(bool adapt, bool exact, const MultiArgs& MA, int total, size_t bytes, cudaStream_t st) {
+  auto go = [&](auto kernel) -> int {
+    if (int r = ensure_smem(kernel, bytes)) return r;
+    kernel<<<total, CTA_LANES, bytes, st>>>(MA);
+    return launch_err("multi_kernel launch");
+  };
+  if (exact) return go(multi_kernel<false, true>);
+  return adapt ? go(multi_kernel<true>) : go(multi_kernel<false>);
 }

@@ -33,12 +33,12 @@ METRIC = "grasps/s (200-step runs) & QP solves/s at 1e-5 residual; p50/p99 job l
 WORKLOAD = "paper-scale: 4096 grasps, 5-finger 22-joint hand, 5 contacts, 64^3 SDF grid (2 mm), " \
            "12 wrenches, 200 upper steps x 50 ADMM iterations, fp32"
 N_STEPS, ADMM_ITERS, B_PER_GPU, S = 200, 50, 4096, 12
-SM_COUNT, FP32_LANES = 152, 128
+FP32_LANES = 128  # FP32 FMA lanes per SM (Blackwell)
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused_kernel<5, step> launch on this
-# workload (profiles/fused_step_paper_4096.md; a 5-step launch of the same kernel -- the state
-# is read once per launch and the grid stays in L2, so the bytes do not grow with the steps)
+# workload, from an ncu capture of a 5-step launch of the same kernel (the state is read once
+# per launch and the grid stays in L2, so the bytes do not grow with the steps)
 TRAFFIC_BYTES = 14_551_040 + 2_304
-TRAFFIC_SOURCE = "ncu capture in profiles/fused_step_paper_4096.md (5-step launch; per-launch bytes)"
+TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum of one fused_kernel<5, step> launch (5 steps)"
 
 
 def admm_iter_flops(m: int) -> int:
@@ -60,8 +60,14 @@ def flops_per_grasp_step(m: int, n_joints: int, s: int, iters: int) -> float:
     return s * iters * f_it + setup
 
 
+def sm_count() -> int:
+    """Streaming multiprocessors of the current device (152 on a GB300)."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
 def fp32_peak_tflops(sm_mhz: float) -> float:
-    return SM_COUNT * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+    return sm_count() * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -128,54 +134,84 @@ def measured_peaks():
 
 
 # ---------------------------------------------------------------------------- CPU oracle
-def oracle_rate(sample_grasps: int, sample_steps: int, seed: int, threads: int | None = None):
-    """The FP64 oracle's coarse-stage loop (central-difference gradient, its
-    default) on the first `sample_grasps` grasps for `sample_steps` upper
-    iterations; returns (grasps/s for 200-step runs, seconds, threads)."""
+def oracle_run(wl: str, grasps: int, steps: int, grad_mode: str = "analytic", threads: int | None = None):
+    """One measured run of the FP64 oracle's coarse-stage loop (exact
+    active-set QPs; the analytic envelope gradient, or central differences):
+    the first `grasps` grasps of workload `wl` for `steps` upper iterations.
+    Returns (grasps/s for runs of that length, seconds, threads)."""
     import oracle as O
-    hand = I.hand_template("hand5")
-    obj = I.grid_object(2)
-    x0 = I.initial_poses(hand, obj, sample_grasps, seed)
-    T, P = I.wrench_set(S), I.default_params()
-    H, Ob = O.Hand(hand), O.Object(obj)
+    hand, obj, x0, T, P, _, _ = I.workload(wl, batch=grasps)
     th = threads or O.default_threads()
+    H, Ob = O.Hand(hand), O.Object(obj)
     t0 = time.perf_counter()
-    O.run(H, Ob, x0, T, P, n_steps=sample_steps, grad_mode="fd", threads=th)
+    O.run(H, Ob, x0, T, P, n_steps=steps, grad_mode=grad_mode, threads=th)
     dt = time.perf_counter() - t0
-    return sample_grasps * sample_steps / N_STEPS / dt, dt, th
+    return grasps / dt, dt, th
 
 
-def calibrated_oracle_sample(target_s: float, seed: int):
+def paper_sample_size(budget_s: float, threads: int, cap: int = 256) -> int:
+    """Grasps of the paper workload whose 200-step oracle run takes about
+    `budget_s` on `threads` threads (a multiple of the threads, at most
+    `cap`), from a 2-step probe."""
+    rate, _, _ = oracle_run("paper", threads, 2, threads=threads)  # grasps/s for 2-step runs
+    g = int(budget_s * rate * 2 / N_STEPS)
+    return max(threads, min(cap, g // threads * threads))
+
+
+def cpu_baseline(budget_s: float):
+    """The oracle on the host cores: the paper workload (config 2) as one
+    measured 200-step run of up to 256 grasps; the tiny workload (config 1)
+    in full, 64 grasps x 50 steps; the differentiation workload (config 3)
+    in full: the evaluation of its 1024 grasps plus central differences
+    (h = 1e-6) on its 64 sampled instances; and config 2 on one core."""
     import oracle as O
     th = O.default_threads()
-    probe = max(th, 4)
-    _, dt, _ = oracle_rate(probe, 1, seed, th)
-    per_grasp_step = dt / probe
-    g = int(max(th, min(4096, target_s / max(per_grasp_step, 1e-6))))
-    g = max(th, (g // th) * th)
-    return oracle_rate(g, 1, seed, th), g
+    g = paper_sample_size(budget_s, th)
+    rate, dt, _ = oracle_run("paper", g, N_STEPS, threads=th)
+    r1, dt1, _ = oracle_run("tiny", 64, 50, threads=th)
+    hand, obj, x0, T, P, _, _ = I.workload("grad")
+    idx = np.random.default_rng(3).choice(1024, 64, replace=False)
+    t0 = time.perf_counter()
+    O.evaluate(O.Hand(hand), O.Object(obj), x0, T, P, threads=th)
+    O.grad_fd(O.Hand(hand), O.Object(obj), x0[idx], T, P, step=1e-6, threads=th)
+    dt3 = time.perf_counter() - t0
+    g1 = 2
+    rate_1, dt_1, _ = oracle_run("paper", g1, N_STEPS, threads=1)
+    return {"value": rate, "unit": "grasps/s", "cores": th, "kind": "oracle",
+            "sample": f"paper workload, {g} grasps x {N_STEPS} upper steps (one measured run, exact active-set QPs, "
+                      f"analytic envelope gradient), {dt:.1f} s on {th} threads",
+            "single_core": {"value": rate_1, "unit": "grasps/s", "cores": 1,
+                            "sample": f"{g1} grasps x {N_STEPS} upper steps, {dt_1:.1f} s"},
+            "tiny_config_full": {"value": r1, "unit": "grasps/s", "sample": f"64 grasps x 50 upper steps, {dt1:.1f} s"},
+            "differentiation_config_full": {"seconds": dt3,
+                                            "sample": "1024-grasp evaluation + central differences (h = 1e-6) on 64 "
+                                                      "sampled grasps"},
+            "paper_context": "49.8 grasps/s for the whole pipeline on one RTX 3090 (Shadow hand, Table 3); "
+                             "context only, another machine and pipeline"}
 
 
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    rates = []
-    (rate, dt, th), sample = calibrated_oracle_sample(8.0, seed=2)
+    import oracle as O
+    th = O.default_threads()
+    g = paper_sample_size(6.0, th, cap=128)
+    rates, secs = [], []
     for k in range(args.warmup + args.steps):
-        if k > 0:
-            rate, dt, th = oracle_rate(sample, 1, 2)
+        rate, dt, _ = oracle_run("paper", g, N_STEPS, threads=th)
         if k >= args.warmup:
-            rates.append((rate, dt))
-    value = float(np.mean([r for r, _ in rates]))
-    ms = float(np.mean([d for _, d in rates]) * 1e3)
+            rates.append(rate)
+            secs.append(dt)
+    value = float(np.mean(rates))
+    ms = float(np.mean(secs) * 1e3)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "grasps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "sample": f"{sample} grasps x 1 upper step per bench step"},
+        "config": {"workload": WORKLOAD, "sample": f"{g} grasps x {N_STEPS} upper steps per bench step"},
         "cpu_baseline": {"value": value, "unit": "grasps/s", "cores": th, "kind": "oracle",
-                         "sample": f"{sample} grasps x 1 upper step (central-difference gradient), "
-                                   f"scaled to 200-step runs"},
+                         "sample": f"paper workload, {g} grasps x {N_STEPS} upper steps per bench step (measured "
+                                   f"200-step runs, exact active-set QPs, analytic envelope gradient)"},
         "e2e": {"value": value, "unit": "grasps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -289,6 +325,7 @@ def run_ours(args, rank, world, local_rank):
         extra["admm_sweep"] = admm_sweep(bx, torch, H, Ob, x_dev, T_dev, P, B)
         extra["synthesis"] = synthesis_rate(bx, torch, H, Ob, x_dev, T_dev, sp)
         extra["energies"] = energy_variants(bx, torch, H, Ob, x_dev, T_dev, P)
+        extra["exact_qps_200_steps"] = exact_run_rate(bx, torch, H, Ob, x_dev, T_dev, P)
         # the pyramid's QPs with the default fixed penalty; adaptive rho beside it
         extra["qp_solves"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev)
         extra["qp_solves"]["adaptive_rho"] = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev, adaptive_rho=1)
@@ -301,17 +338,7 @@ def run_ours(args, rank, world, local_rank):
         if args.serve_jobs > 0:
             extra["serving"] = serving_latency(bx, torch, P, args.serve_jobs)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        (cpu_rate, cpu_dt, cores), g = calibrated_oracle_sample(args.cpu_seconds, seed=2)
-        # the same oracle on one core, on a sample of the same per-core size
-        g1 = max(1, g // max(cores, 1))
-        rate1, dt1, _ = oracle_rate(g1, 1, 2, 1)
-        extra["cpu_baseline"] = {"value": cpu_rate, "unit": "grasps/s", "cores": cores, "kind": "oracle",
-                                 "sample": f"{g} grasps x 1 upper step of the same workload (central-difference "
-                                           f"gradient, exact active-set QPs), {cpu_dt:.1f} s, scaled to 200-step runs",
-                                 "single_core": {"value": rate1, "unit": "grasps/s", "cores": 1,
-                                                 "sample": f"{g1} grasps x 1 upper step, {dt1:.1f} s"},
-                                 "paper_context": "49.8 grasps/s for the whole pipeline on one RTX 3090 (Shadow hand, "
-                                                  "Table 3); context only, another machine and pipeline"}
+        extra["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if rank != 0:
         return
     line = {
@@ -325,7 +352,7 @@ def run_ours(args, rank, world, local_rank):
                      "frac": achieved / peak, "traffic": TRAFFIC_BYTES if n_up == N_STEPS else None,
                      "traffic_source": TRAFFIC_SOURCE,
                      "kernel": "fused_kernel<5, step> (one launch per 200-step run)",
-                     "peak_source": f"FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x {sm_max:.0f} MHz",
+                     "peak_source": f"FP32 FMA: {sm_count()} SMs x 128 lanes x 2 FLOP x {sm_max:.0f} MHz",
                      "kernel_ms": float(np.mean(kern_ms)), "alg_flops_per_launch": fl},
         "gpu_launches": args.steps,
         "clocks": clocks,
@@ -336,7 +363,7 @@ def run_ours(args, rank, world, local_rank):
         line["e2e"] = extra.pop("e2e")
     line.update(extra)
     if "serving" in line:
-        sv = line["serving"]["residual_1e-5"]
+        sv = line["serving"]["exact_qps"]
         cb, pl = sv["continuous_batching"], sv["plain_per_job"]
         line["p50_job_latency_s"], line["p99_job_latency_s"] = cb["p50_s"], cb["p99_s"]
         line["p50_p99_job_latency_plain_per_job_s"] = [pl["p50_s"], pl["p99_s"]]
@@ -362,10 +389,14 @@ def _timed(torch, fn, reps=3):
 def persistent_mixed(bx, torch, P):
     """Mixed-template batch (3-finger/3-contact, 4-finger/4-contact,
     5-finger/5-contact hands; 512 / 2048 / 6144 grasps over six grids of
-    48-96 nodes), 200 upper steps x 50 ADMM iterations, four ways:
-    one persistent launch for all jobs; one launch per job and upper step;
-    that per-step loop captured once in a CUDA graph and replayed; and the
-    persistent launch with the autotuner's CTA tile and ADMM schedule."""
+    48-96 nodes), 200 upper steps: one persistent launch for all jobs; one
+    launch per job and upper step; that per-step loop captured once in a
+    CUDA graph and replayed -- each with 50 ADMM iterations per step and
+    with every QP of every step solved exactly (qp.solver = EXACT: every
+    QP at a Frank-Wolfe gap, an upper bound on Q - Q*, of 1e-5 Q + 1e-7,
+    which is tighter than a 1e-5 ADMM residual); and the persistent launch
+    with the autotuner's pick under each of its two rules (final energy;
+    every QP at 1e-5 on 99% of the grasps)."""
     from paper_2412_16490_gb300.autotune import autotune, tuned_params
     jobs, T = I.mixed_workload(seed=4)
     Tt = torch.as_tensor(T).cuda()
@@ -388,83 +419,84 @@ def persistent_mixed(bx, torch, P):
         reset()
         bx.bodex_step_multi([dict(j, n_steps=N_STEPS) for j in J], params)
 
-    def per_step():
+    def per_step(params):
         for _ in range(N_STEPS):
             for j in J:
-                bx.bodex_step(j["hand"], j["obj"], j["state"], Tt, 1, sp)
+                bx.bodex_step(j["hand"], j["obj"], j["state"], Tt, 1, params)
 
-    def plain():
+    def frac_le(lim):
+        return float((torch.cat([j["state"].residual() for j in J]) <= lim).float().mean().item())
+
+    def three_forms(params):
+        ms_p = _timed(torch, lambda: persistent(params))
+        frac_p = frac_le(1e-5)
+
+        def plain():
+            reset()
+            per_step(params)
+
+        ms_l = _timed(torch, plain, reps=2)
+        frac_l = frac_le(1e-5)
         reset()
-        per_step()
-
-    ms_persistent = _timed(torch, lambda: persistent(sp))
-    ms_plain = _timed(torch, plain, reps=2)
-    reset()
-    per_step()  # warm-up outside the capture
-    torch.cuda.synchronize()
-    g = torch.cuda.CUDAGraph()
-    reset()
-    with torch.cuda.graph(g):
-        per_step()
-
-    def graph():
+        per_step(params)  # warm-up outside the capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
         reset()
-        g.replay()
+        with torch.cuda.graph(g):
+            per_step(params)
 
-    ms_graph = _timed(torch, graph)
-    # the same two forms with every QP solved to a 1e-5 residual (cap 200, warm-started)
-    sp_res = bx.step_params(P, qp=bx.qp_params(eps_abs=1e-5, max_iter=200, check_every=10))
-    ms_res_persistent = _timed(torch, lambda: persistent(sp_res))
-    res_persistent = torch.cat([j["state"].residual() for j in J])
+        def graph():
+            reset()
+            g.replay()
 
-    def plain_res():
-        reset()
-        for _ in range(N_STEPS):
-            for j in J:
-                bx.bodex_step(j["hand"], j["obj"], j["state"], Tt, 1, sp_res)
+        ms_g = _timed(torch, graph)
+        return {"persistent": {"ms": ms_p, "grasps_per_s": grasps / ms_p * 1e3, "launches": 1,
+                               "frac_grasps_all_qps_le_1e-5": frac_p},
+                "per_step_launches": {"ms": ms_l, "grasps_per_s": grasps / ms_l * 1e3, "launches": N_STEPS * len(J),
+                                      "frac_grasps_all_qps_le_1e-5": frac_l},
+                "per_step_cuda_graph": {"ms": ms_g, "grasps_per_s": grasps / ms_g * 1e3,
+                                        "launches": N_STEPS * len(J)}}
 
-    ms_res_plain = _timed(torch, plain_res, reps=2)
+    out = {"grasps": grasps, "jobs": len(J), "upper_steps": N_STEPS}
+    fixed = three_forms(sp)
+    out.update(fixed)  # 50 ADMM iterations per step
+    out["exact_qps"] = three_forms(bx.step_params(P, qp=bx.qp_params(max_iter=64, solver=bx.QP_EXACT)))
     big = max(J, key=lambda j: j["x0"].shape[0])
-    t0 = time.perf_counter()
     # tuned on the largest job at its full size: the best CTA tile depends on
     # how many CTAs the launch spreads over the SMs, so a small sample misleads
-    tuned = autotune(big["hand"], big["obj"], big["x0"], Tt, P, steps=N_STEPS)
-    tune_s = time.perf_counter() - t0
-    ms_tuned = _timed(torch, lambda: persistent(tuned_params(tuned, P)))
-    res = torch.cat([j["state"].residual() for j in J])
-    return {"grasps": grasps, "jobs": len(J), "upper_steps": N_STEPS,
-            "persistent": {"ms": ms_persistent, "grasps_per_s": grasps / ms_persistent * 1e3, "launches": 1},
-            "per_step_launches": {"ms": ms_plain, "grasps_per_s": grasps / ms_plain * 1e3,
-                                  "launches": N_STEPS * len(J)},
-            "per_step_cuda_graph": {"ms": ms_graph, "grasps_per_s": grasps / ms_graph * 1e3,
-                                    "launches": N_STEPS * len(J)},
-            "residual_1e-5": {"persistent": {"ms": ms_res_persistent,
-                                             "grasps_per_s": grasps / ms_res_persistent * 1e3,
-                                             "frac_res_le_1e-5": float((res_persistent <= 1e-5).float().mean().item())},
-                              "per_step_launches": {"ms": ms_res_plain, "grasps_per_s": grasps / ms_res_plain * 1e3}},
-            "autotuned_persistent": {"ms": ms_tuned, "grasps_per_s": grasps / ms_tuned * 1e3,
-                                     "grasps_per_cta": tuned["grasps_per_cta"], "schedule": tuned["schedule"],
-                                     "sample_median_E": tuned["median_E"],
-                                     "sample_reference_median_E": tuned["reference_median_E"],
-                                     "frac_res_le_1e-5": float((res <= 1e-5).float().mean().item()),
-                                     "tune_s": tune_s}}
+    for label, rule in (("autotuned_energy", None), ("autotuned_residual_1e-5", 1e-5)):
+        t0 = time.perf_counter()
+        tuned = autotune(big["hand"], big["obj"], big["x0"], Tt, P, steps=N_STEPS, residual=rule)
+        tune_s = time.perf_counter() - t0
+        ms_tuned = _timed(torch, lambda: persistent(tuned_params(tuned, P)))
+        out[label] = {"ms": ms_tuned, "grasps_per_s": grasps / ms_tuned * 1e3,
+                      "grasps_per_cta": tuned["grasps_per_cta"], "schedule": tuned["schedule"],
+                      "rule": "median final energy within 1% of 50 ADMM iterations" if rule is None else
+                              "every QP at <= 1e-5 on >= 99% of the grasps",
+                      "tuning_job_median_E": tuned["median_E"], "tuning_job_reference_median_E": tuned["reference_median_E"],
+                      "frac_grasps_all_qps_le_1e-5": frac_le(1e-5), "tune_s": tune_s,
+                      "candidates": [dict(tile=t["tile"], schedule=t["schedule"], ms=t["ms"], ok=t["ok"],
+                                          frac_res_le_1e5=t["frac_res_le_1e5"]) for t in tuned["table"]]}
+    return out
 
 
 def serving_latency(bx, torch, P, n_jobs):
     """Poisson arrivals (20 jobs/s, seeded) of jobs with 32-128^3 grids, one of
     the three hand templates and 256-4096 grasps x 200 steps, served by the
     continuous-batching server and by one-job-at-a-time per-step launches,
-    both with the QPs solved to a 1e-5 residual (the comparison's setting;
-    cap 200 iterations, warm-started) and with the fixed 50 iterations of
-    the bench line."""
+    both with every QP of every step solved exactly (qp.solver = EXACT, each
+    QP's Frank-Wolfe gap <= 1e-5 Q + 1e-7: the comparison at a QP accuracy
+    of at least 1e-5) and with the fixed 50 ADMM iterations of the bench
+    line; the fraction of grasps whose QPs all ended at <= 1e-5 is reported
+    with each."""
     from paper_2412_16490_gb300.serving import PlainServer, PoissonWorkload, Server, latency_stats
     t0 = time.perf_counter()
     specs = PoissonWorkload(n_jobs=n_jobs, rate=20.0, seed=5).build()
     build_s = time.perf_counter() - t0
     out = {"arrival_rate_per_s": 20.0, "jobs": n_jobs, "workload_build_s": build_s}
     warm = PoissonWorkload(n_jobs=3, rate=1000.0, seed=6, grid_choices=(32,), grasp_choices=(256,), n_steps=20).build()
-    for label, qp in (("residual_1e-5", bx.qp_params(eps_abs=1e-5, max_iter=200, check_every=10)),
-                      ("fixed_50_iters", bx.qp_params(max_iter=ADMM_ITERS))):
+    exact = bx.qp_params(max_iter=64, solver=bx.QP_EXACT)
+    for label, qp in (("exact_qps", exact), ("fixed_50_iters", bx.qp_params(max_iter=ADMM_ITERS))):
         Server(P, qp=qp).replay(warm, realtime=False)  # load the kernels
         srv = Server(P, qp=qp, steps_per_tick=10)
         cont = latency_stats(srv.replay(specs, realtime=True))
@@ -473,8 +505,8 @@ def serving_latency(bx, torch, P, n_jobs):
         plain = latency_stats(pl.replay(specs, realtime=True))
         plain.update(launches=pl.launches)
         out[label] = {"continuous_batching": cont, "plain_per_job": plain}
-    # saturated load: the first 60 jobs all submitted at once (1e-5 residual)
-    qp = bx.qp_params(eps_abs=1e-5, max_iter=200, check_every=10)
+    # saturated load: the first 60 jobs all submitted at once (exact QPs)
+    qp = exact
     burst = specs[:60]
     for sp in burst:
         sp.arrival = 0.0
@@ -484,7 +516,7 @@ def serving_latency(bx, torch, P, n_jobs):
     bp = PlainServer(P, qp=qp)
     b_plain = latency_stats(bp.replay(burst, realtime=False))
     b_plain.update(launches=bp.launches)
-    out["burst_60_jobs_residual_1e-5"] = {"continuous_batching": b_cont, "plain_per_job": b_plain}
+    out["burst_60_jobs_exact_qps"] = {"continuous_batching": b_cont, "plain_per_job": b_plain}
     return out
 
 
@@ -539,6 +571,34 @@ def synthesis_rate(bx, torch, H, Ob, x_dev, T_dev, sp, reps=2):
             "grasps_per_s": x_dev.shape[0] / (ms / 1e3),
             "cdc_mm_median": float(np.median(cdc_mm)), "cdc_mm_p90": float(np.percentile(cdc_mm, 90)),
             "fingertip_penetration_mm_median": float(np.median(np.maximum(0.0, -d_mm.min(1))))}
+
+
+def exact_run_rate(bx, torch, H, Ob, x_dev, T_dev, P, reps=3):
+    """The bench workload's 200-step run with every QP of every step solved
+    exactly (qp.solver = EXACT, warm-started from the previous step's working
+    set), beside ADMM to a 1e-5 residual in the loop (cap 1000, warm-started)."""
+    B = int(x_dev.shape[0])
+    st = bx.State(H, B, S)
+    E = torch.empty(B, device="cuda")
+    out = {}
+    for name, qp, r in (("exact", bx.qp_params(max_iter=64, solver=bx.QP_EXACT), reps),
+                        ("admm_to_1e-5_cap_1000", bx.qp_params(eps_abs=1e-5, max_iter=1000, check_every=10), 1)):
+        sp = bx.step_params(P, qp=qp)
+        ts = []
+        for k in range(r + 1):
+            st.set_pose(x_dev)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            bx.bodex_step(H, Ob, st, T_dev, N_STEPS, sp, E_last=E)
+            b.record()
+            torch.cuda.synchronize()
+            if k:
+                ts.append(a.elapsed_time(b))
+        ms = float(np.median(ts))
+        out[name] = {"ms": ms, "grasps_per_s": B / (ms / 1e3), "E_last_median": float(E.median().item()),
+                     "frac_grasps_all_qps_le_1e-5": float((st.residual() <= 1e-5).float().mean().item())}
+    return out
 
 
 def energy_variants(bx, torch, H, Ob, x_dev, T_dev, P, reps=3):
@@ -752,7 +812,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=30.0,
+                    help="time budget of the paper-workload oracle run in the CPU baseline")
     ap.add_argument("--quick", action="store_true", help="skip the QP and e2e side measurements")
     ap.add_argument("--serve-jobs", type=int, default=300, help="jobs in the serving measurement (0 skips it)")
     ap.add_argument("--qp-only", action="store_true", help="only the standalone QP measurement (profiler captures)")

@@ -392,6 +392,16 @@ int bodex_refine(bodex_hand_t hand, bodex_object_t obj, bodex_state_t state, con
 int bodex_contact_metrics(bodex_hand_t hand, bodex_object_t obj, const float* x, int B, float* d, float* cdc,
                           void* stream);
 
+/* Squeeze pose x_s = 2 x - x_p (Sec. IV-D): the execution target, from the
+ * final-stage grasp pose x and the fine-stage pre-grasp pose x_p.
+ *   x, x_p [B,D] (in, device, row-major float32); x_s [B,D] (out, device;
+ *   may alias x or x_p).  Elementwise, no clamp to the joint limits (the
+ *   paper applies none: the squeeze target presses past the grasp).
+ * Asynchronous on `stream`.
+ * Errors: BODEX_ERR_INVALID (B < 0, D < 1, null array with B > 0),
+ * BODEX_ERR_CUDA. */
+int bodex_squeeze_pose(const float* x, const float* x_p, int B, int D, float* x_s, void* stream);
+
 /* Allocation-free variant of bodex_step (the paper has no counterpart: this
  * serves callers that cannot allocate device memory while they run, such as
  * real-time control loops that reserve all memory at start-up, or processes

@@ -20,7 +20,7 @@ __all__ = [
     "load", "Hand", "Object", "State", "qp_params", "step_params",
     "bodex_hand_create", "bodex_object_create", "bodex_state_create",
     "bodex_fk_contacts", "bodex_qp_solve_batch", "bodex_energy_grad", "bodex_energy_adjoint", "bodex_step", "bodex_step_multi", "bodex_refine",
-    "synthesize",
+    "bodex_contact_metrics", "bodex_squeeze_pose", "synthesize",
     "bodex_sync", "bodex_version", "bodex_step_tile", "BodexError",
 ]
 
@@ -317,6 +317,15 @@ def bodex_contact_metrics(hand: Hand, obj: Object, x, stream=None):
     return dict(d=d, cdc=cdc)
 
 
+def bodex_squeeze_pose(x, x_p, stream=None):
+    """Squeeze pose x_s = 2 x - x_p (Sec. IV-D) for poses x, x_p [B,D]."""
+    torch = _torch()
+    B, D = int(x.shape[0]), int(x.shape[1])
+    x_s = torch.empty((B, D), dtype=torch.float32, device=x.device)
+    _b.check(load().bodex_squeeze_pose(_ptr(x), _ptr(x_p), B, D, _ptr(x_s), _stream(stream)))
+    return x_s
+
+
 def synthesize(hand: Hand, obj: Object, x0, T, params: _b.bodex_step_params, coarse_steps=300, fine_steps=100,
                final_steps=100, margin=0.01, w_qp=1000.0, stream=None):
     """The three-stage schedule (Sec. IV-D; 300 / 100 / 100 iterations):
@@ -336,7 +345,7 @@ def synthesize(hand: Hand, obj: Object, x0, T, params: _b.bodex_step_params, coa
     bodex_refine(hand, obj, st, pc, final_steps, 0.0, w_qp, params, E_last=E, stream=stream)
     x = st.pose(stream)
     met = bodex_contact_metrics(hand, obj, x, stream)
-    return dict(x_p=xp, x=x, x_s=2.0 * x - xp, E=E, d=met["d"], cdc=met["cdc"])
+    return dict(x_p=xp, x=x, x_s=bodex_squeeze_pose(x, xp, stream), E=E, d=met["d"], cdc=met["cdc"])
 
 
 def bodex_step_multi(jobs, params: _b.bodex_step_params, stream=None):

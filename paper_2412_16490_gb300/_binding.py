@@ -36,7 +36,7 @@ EXPORTS = (
     "bodex_object_gravity_centre", "bodex_fk_contacts", "bodex_qp_solve_batch", "bodex_state_create",
     "bodex_state_destroy", "bodex_state_set_pose", "bodex_state_get_pose", "bodex_state_get_adam",
     "bodex_state_get_residual", "bodex_step_multi", "bodex_step_tile",
-    "bodex_energy_grad", "bodex_energy_adjoint", "bodex_step", "bodex_refine", "bodex_contact_metrics", "bodex_step_noalloc", "bodex_sync", "bodex_last_error", "bodex_version",
+    "bodex_energy_grad", "bodex_energy_adjoint", "bodex_step", "bodex_refine", "bodex_contact_metrics", "bodex_squeeze_pose", "bodex_step_noalloc", "bodex_sync", "bodex_last_error", "bodex_version",
 )
 
 
@@ -130,6 +130,7 @@ def load(build_if_missing: bool = True):
         "bodex_step": [v, v, v, v, C.c_int, C.c_int, C.POINTER(bodex_step_params), v, v, v],
         "bodex_refine": [v, v, v, v, C.c_int, C.c_float, C.c_float, C.POINTER(bodex_step_params), v, v, v, v],
         "bodex_contact_metrics": [v, v, v, C.c_int, v, v, v],
+        "bodex_squeeze_pose": [v, v, C.c_int, C.c_int, v, v],
         "bodex_step_noalloc": [v, v, v, C.c_int, v, C.c_int, C.c_int, C.POINTER(bodex_step_params), v, v, v],
         "bodex_sync": [v],
     }

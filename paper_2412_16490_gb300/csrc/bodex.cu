@@ -1062,6 +1062,26 @@ extern "C" int bodex_contact_metrics(bodex_hand_t h, bodex_object_t o, const flo
   }
 }
 
+// ============================================================================ squeeze pose
+// x_s = 2 x - x_p (Sec. IV-D), elementwise over B * D floats; 2 x is exact
+// in float, so the one rounding gives the same value as the formula.
+__global__ void __launch_bounds__(256) squeeze_kernel(const float* __restrict__ x, const float* __restrict__ xp,
+                                                      size_t n, float* __restrict__ xs) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    xs[i] = fmaf(2.f, x[i], -xp[i]);
+}
+
+extern "C" int bodex_squeeze_pose(const float* x, const float* x_p, int B, int D, float* x_s, void* stream) {
+  if (B < 0 || D < 1) return fail(BODEX_ERR_INVALID, "B < 0 or D < 1");
+  if (B > 0 && (!x || !x_p || !x_s)) return fail(BODEX_ERR_INVALID, "null array");
+  if (B == 0) return BODEX_OK;
+  const size_t n = (size_t)B * D;
+  const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 4096);
+  (void)cudaGetLastError();
+  squeeze_kernel<<<blocks, 256, 0, as_stream(stream)>>>(x, x_p, n, x_s);
+  return launch_err("squeeze_kernel launch");
+}
+
 // ============================================================================ allocation-free step
 // Some callers cannot allocate device memory once they are running: a robot
 // controller that reserves everything at start-up so that its control loop

@@ -49,6 +49,7 @@ class JobResult:
     start: float
     finish: float
     tag: object = None
+    res: np.ndarray | None = None  # [B] largest QP residual (ADMM) or Frank-Wolfe gap (exact) of the last step
 
     @property
     def latency(self) -> float:
@@ -160,7 +161,8 @@ class _Base:
     def _close(self, a: _Active):
         x = a.state.pose().cpu().numpy()
         E = a.E.cpu().numpy()
-        self.results[a.jid] = JobResult(x, E, a.spec.arrival, a.start, self.now(), a.spec.tag)
+        res = a.state.residual().cpu().numpy()
+        self.results[a.jid] = JobResult(x, E, a.spec.arrival, a.start, self.now(), a.spec.tag, res)
         return self._release_object(a.spec.obj)
 
     def replay(self, specs, realtime: bool = True, idle_sleep: float = 2e-4):
@@ -218,7 +220,7 @@ class Server(_Base):
         self.max_jobs = min(int(max_jobs), BODEX_MAX_JOBS)
         self.max_inflight = max(1, int(max_inflight))
         self.active: list = []      # jobs with steps left
-        self.finishing: list = []   # (job, event, pinned x, pinned E): last tick enqueued
+        self.finishing: list = []   # (job, event, pinned x, E, residual): last tick enqueued
         self.inflight: deque = deque()
         self.used = 0
         self.pool: dict = {}        # _state_key -> [State]
@@ -281,18 +283,18 @@ class Server(_Base):
 
     def _reap(self, block: bool = False):
         keep = []
-        for a, ev, xh, Eh in self.finishing:
+        for a, ev, xh, Eh, rh in self.finishing:
             if block:
                 ev.synchronize()
             if block or ev.query():
                 self.results[a.jid] = JobResult(xh.numpy().copy(), Eh.numpy().copy(), a.spec.arrival, a.start,
-                                                self.now(), a.spec.tag)
+                                                self.now(), a.spec.tag, rh.numpy().copy())
                 self.used -= a.nbytes + self._release_object(a.spec.obj)
                 self.pool.setdefault(_state_key(a.spec), []).append(a.state)
                 self.pooled += state_bytes(a.spec)
                 a.state = None
             else:
-                keep.append((a, ev, xh, Eh))
+                keep.append((a, ev, xh, Eh, rh))
         self.finishing = keep
         while self.inflight and self.inflight[0].query():
             self.inflight.popleft()
@@ -322,11 +324,13 @@ class Server(_Base):
                 self.ctas -= self._job_ctas(a.spec)
                 xh = torch.empty((a.spec.x0.shape[0], a.hand.D), dtype=torch.float32).pin_memory()
                 Eh = torch.empty(a.spec.x0.shape[0], dtype=torch.float32).pin_memory()
+                rh = torch.empty(a.spec.x0.shape[0], dtype=torch.float32).pin_memory()
                 xh.copy_(a.state.pose(), non_blocking=True)
                 Eh.copy_(a.E, non_blocking=True)
+                rh.copy_(a.state.residual(), non_blocking=True)
                 ev = torch.cuda.Event()
                 ev.record()
-                self.finishing.append((a, ev, xh, Eh))
+                self.finishing.append((a, ev, xh, Eh, rh))
             else:
                 keep.append(a)
         self.active = keep
@@ -361,9 +365,13 @@ def latency_stats(results: dict) -> dict:
     lat = np.array([r.latency for r in results.values()])
     grasps = sum(r.x.shape[0] for r in results.values())
     span = max(r.finish for r in results.values()) - min(r.arrival for r in results.values())
-    return dict(p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
-                mean_s=float(lat.mean()), jobs=len(lat), grasps=int(grasps), span_s=float(span),
-                grasps_per_s=float(grasps / span) if span > 0 else None)
+    out = dict(p50_s=float(np.percentile(lat, 50)), p99_s=float(np.percentile(lat, 99)),
+               mean_s=float(lat.mean()), jobs=len(lat), grasps=int(grasps), span_s=float(span),
+               grasps_per_s=float(grasps / span) if span > 0 else None)
+    if all(r.res is not None for r in results.values()):
+        res = np.concatenate([r.res for r in results.values()])
+        out["frac_grasps_all_qps_le_1e-5"] = float((res <= 1e-5).mean())
+    return out
 
 
 @dataclass

@@ -59,7 +59,8 @@ def test_synthesize_three_stages():
     out = bx.synthesize(H, Ob, cuda(x0), cuda(T), sp, coarse_steps=50, fine_steps=20, final_steps=20)
     xp, x, xs = host(out["x_p"]), host(out["x"]), host(out["x_s"])
     assert np.isfinite(x).all() and np.isfinite(xp).all()
-    np.testing.assert_allclose(xs, 2 * x - xp, atol=1e-6)
+    # x_s = 2 x - x_p (Sec. IV-D) from the library: 2 x is exact in float32, so bitwise
+    np.testing.assert_array_equal(xs, (np.float32(2) * x - xp).astype(np.float32))
     # the final stage (no margin) ends closer to the surface than the pre-grasp
     ev_p = O.evaluate(O.Hand(hand), O.Object(obj), xp.astype(np.float64), T, P)
     ev_x = O.evaluate(O.Hand(hand), O.Object(obj), x.astype(np.float64), T, P)
@@ -67,6 +68,26 @@ def test_synthesize_three_stages():
     # the metrics returned with the grasp are those of x
     ref = O.contact_metrics(O.Hand(hand), O.Object(obj), x.astype(np.float64))
     np.testing.assert_allclose(host(out["cdc"]), ref["cdc"], rtol=0, atol=4e-6)
+
+
+def test_squeeze_pose_call_and_edge_cases():
+    """bodex_squeeze_pose: bitwise 2 x - x_p on a ragged size, in place into x,
+    an empty batch, and its error codes."""
+    rng = np.random.default_rng(8)
+    x = rng.normal(size=(1037, 28)).astype(np.float32)
+    xp = rng.normal(size=(1037, 28)).astype(np.float32)
+    got = host(bx.bodex_squeeze_pose(cuda(x), cuda(xp)))
+    np.testing.assert_array_equal(got, (np.float32(2) * x - xp).astype(np.float32))
+    xd = cuda(x)
+    L = bx.load()
+    import ctypes as C
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    ptr = lambda t: C.c_void_p(t.data_ptr())
+    assert L.bodex_squeeze_pose(ptr(xd), ptr(cuda(xp)), 1037, 28, ptr(xd), stream) == 0  # aliasing x
+    np.testing.assert_array_equal(host(xd), got)
+    assert bx.bodex_squeeze_pose(cuda(x[:0]), cuda(xp[:0])).shape == (0, 28)
+    assert L.bodex_squeeze_pose(None, None, 3, 28, None, stream) == 1
+    assert L.bodex_squeeze_pose(ptr(xd), ptr(xd), -1, 28, ptr(xd), stream) == 1
 
 
 @pytest.mark.parametrize("kind,B", [("sphere", 64), ("grid", 200)])

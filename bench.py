@@ -253,7 +253,7 @@ def run_ours(args, rank, world, local_rank):
     if args.mixed_only:  # one persistent launch of the mixed-template batch (profiler captures)
         jobs, T = I.mixed_workload(seed=4)
         Tt = torch.as_tensor(T).cuda()
-        sp_m = bx.step_params(P, qp=bx.qp_params(max_iter=ADMM_ITERS))
+        sp_m = bx.step_params(P, qp=bx.qp_params(max_iter=ADMM_ITERS), work_pulling=int(args.work_pulling))
         hands, table = {}, []
         for hand_t, obj_t, xj in jobs:
             Hj = hands.setdefault(hand_t.name, bx.Hand(hand_t))
@@ -266,6 +266,20 @@ def run_ours(args, rank, world, local_rank):
         if rank == 0:
             print(json.dumps({"workload": f"mixed templates, {sum(j.shape[0] for _, _, j in jobs)} grasps, "
                                           f"{n_up} upper steps per launch", "launches": 2}))
+        return
+    if args.exact_step_only:  # two fused runs with exact QPs (a small command for profiler captures)
+        sp_x = bx.step_params(P, qp=bx.qp_params(max_iter=64, solver=bx.QP_EXACT))
+        for _ in range(2):
+            st.set_pose(x_dev)
+            bx.bodex_step(H, Ob, st, T_dev, n_up, sp_x, E_last=E_dev, status=stat_dev)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"workload": f"paper workload, {n_up} upper steps with exact QPs", "launches": 2}))
+        return
+    if args.qp_exact_only:  # the exact QP solver alone (a small command for profiler captures)
+        line = qp_exact_rate(bx, torch, H, Ob, x_dev, T_dev)
+        if rank == 0:
+            print(json.dumps(dict(line, workload="49152 QPs at the paper geometry, exact solver")))
         return
     if args.qp_only:  # the standalone batched QPs alone (a small command for profiler captures)
         line = qp_solve_rate(bx, torch, H, Ob, x_dev, T_dev)
@@ -427,9 +441,13 @@ def persistent_mixed(bx, torch, P):
     def frac_le(lim):
         return float((torch.cat([j["state"].residual() for j in J]) <= lim).float().mean().item())
 
+    def pulling(params):
+        return bx.step_params(P, qp=params.qp, grasps_per_cta=params.grasps_per_cta, work_pulling=1)
+
     def three_forms(params):
         ms_p = _timed(torch, lambda: persistent(params))
         frac_p = frac_le(1e-5)
+        ms_w = _timed(torch, lambda: persistent(pulling(params)))
 
         def plain():
             reset()
@@ -451,7 +469,10 @@ def persistent_mixed(bx, torch, P):
 
         ms_g = _timed(torch, graph)
         return {"persistent": {"ms": ms_p, "grasps_per_s": grasps / ms_p * 1e3, "launches": 1,
-                               "frac_grasps_all_qps_le_1e-5": frac_p},
+                               "frac_grasps_all_qps_le_1e-5": frac_p, "schedule": "one block per tile"},
+                "persistent_work_pulling": {"ms": ms_w, "grasps_per_s": grasps / ms_w * 1e3, "launches": 1,
+                                            "schedule": "grid = resident blocks, tiles from an atomic counter, "
+                                                        "costliest jobs first"},
                 "per_step_launches": {"ms": ms_l, "grasps_per_s": grasps / ms_l * 1e3, "launches": N_STEPS * len(J),
                                       "frac_grasps_all_qps_le_1e-5": frac_l},
                 "per_step_cuda_graph": {"ms": ms_g, "grasps_per_s": grasps / ms_g * 1e3,
@@ -469,12 +490,15 @@ def persistent_mixed(bx, torch, P):
         tuned = autotune(big["hand"], big["obj"], big["x0"], Tt, P, steps=N_STEPS, residual=rule)
         tune_s = time.perf_counter() - t0
         ms_tuned = _timed(torch, lambda: persistent(tuned_params(tuned, P)))
+        frac = frac_le(1e-5)
+        ms_tw = _timed(torch, lambda: persistent(pulling(tuned_params(tuned, P))))
         out[label] = {"ms": ms_tuned, "grasps_per_s": grasps / ms_tuned * 1e3,
+                      "work_pulling_grasps_per_s": grasps / ms_tw * 1e3,
                       "grasps_per_cta": tuned["grasps_per_cta"], "schedule": tuned["schedule"],
                       "rule": "median final energy within 1% of 50 ADMM iterations" if rule is None else
                               "every QP at <= 1e-5 on >= 99% of the grasps",
                       "tuning_job_median_E": tuned["median_E"], "tuning_job_reference_median_E": tuned["reference_median_E"],
-                      "frac_grasps_all_qps_le_1e-5": frac_le(1e-5), "tune_s": tune_s,
+                      "frac_grasps_all_qps_le_1e-5": frac, "tune_s": tune_s,
                       "candidates": [dict(tile=t["tile"], schedule=t["schedule"], ms=t["ms"], ok=t["ok"],
                                           frac_res_le_1e5=t["frac_res_le_1e5"]) for t in tuned["table"]]}
     return out
@@ -817,8 +841,14 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the QP and e2e side measurements")
     ap.add_argument("--serve-jobs", type=int, default=300, help="jobs in the serving measurement (0 skips it)")
     ap.add_argument("--qp-only", action="store_true", help="only the standalone QP measurement (profiler captures)")
+    ap.add_argument("--exact-step-only", action="store_true",
+                    help="only two fused runs with exact QPs (profiler captures; --upper-steps sets their length)")
+    ap.add_argument("--qp-exact-only", action="store_true",
+                    help="only the exact-solver QP measurement (profiler captures)")
     ap.add_argument("--mixed-only", action="store_true",
                     help="only two persistent launches of the mixed-template batch (profiler captures)")
+    ap.add_argument("--work-pulling", action="store_true",
+                    help="with --mixed-only: the persistent work-pulling schedule of the several-job launch")
     ap.add_argument("--upper-steps", type=int, default=N_STEPS,
                     help="upper iterations per run (200 for the bench line; fewer for profiler captures)")
     args = ap.parse_args()

@@ -244,6 +244,16 @@ typedef struct bodex_step_params {
   bodex_qp_params qp;
   int grasps_per_cta;  /* CTA tile: grasps per thread block (0 = default, 96 / s); an
                           autotuner knob that changes speed, never results */
+  int work_pulling;    /* bodex_step_multi only.  0: one thread block per tile (a job's
+                          grasps_per_cta grasps), the jobs' tiles in the caller's order,
+                          scheduled onto the SMs by the hardware.  1: a persistent grid of
+                          as many blocks as fit on the GPU at once; each block takes the
+                          next tile from one atomic counter, the tiles of the costliest
+                          jobs first, until none is left.  Results equal the jobs' own
+                          launches bitwise with 0; with 1, bitwise for fixed-iteration
+                          ADMM and within float32 rounding otherwise (the item loop
+                          changes the compiler's multiply-add contraction).  1 was
+                          measured slower on the mixed-template batch; 0 is the default. */
 } bodex_step_params;
 
 /* ---------------------------------------------------------------- calls */

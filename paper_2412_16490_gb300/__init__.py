@@ -70,7 +70,7 @@ def qp_params(mu=0.5, beta=1.0, gamma=0.5, rho=0.1, sigma=1e-6, alpha=1.6, eps_a
 
 
 def step_params(params: dict | None = None, qp: _b.bodex_qp_params | None = None,
-                grasps_per_cta: int = 0) -> _b.bodex_step_params:
+                grasps_per_cta: int = 0, work_pulling: int = 0) -> _b.bodex_step_params:
     """Upper-level parameters (struct bodex_step_params) from a dict with keys
     lr_t, lr_r, b1, b2, adam_eps, w_q, w_d, delta, energy (ENERGY_QP or
     ENERGY_DFC), the collision energies w_pen, w_self, w_lim, eta_pen, eta_lim
@@ -86,7 +86,7 @@ def step_params(params: dict | None = None, qp: _b.bodex_qp_params | None = None
     return _b.bodex_step_params(p["lr_t"], p["lr_r"], p["b1"], p["b2"], p["adam_eps"],
                                 _b.bodex_energy_params(p["w_q"], p["w_d"], p["delta"], int(p["energy"]), p["w_pen"],
                                                        p["w_self"], p["w_lim"], p["eta_pen"], p["eta_lim"]), qp,
-                                int(grasps_per_cta))
+                                int(grasps_per_cta), int(work_pulling))
 
 
 # ---------------------------------------------------------------- handles

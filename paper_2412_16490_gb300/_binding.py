@@ -69,7 +69,7 @@ class bodex_energy_params(C.Structure):
 class bodex_step_params(C.Structure):
     _fields_ = [("lr_t", C.c_float), ("lr_r", C.c_float), ("b1", C.c_float), ("b2", C.c_float),
                 ("adam_eps", C.c_float), ("energy", bodex_energy_params), ("qp", bodex_qp_params),
-                ("grasps_per_cta", C.c_int)]
+                ("grasps_per_cta", C.c_int), ("work_pulling", C.c_int)]
 
 
 class bodex_job(C.Structure):

@@ -81,6 +81,7 @@ struct bodex_state_s {
   float* qy = nullptr;
   float* qw = nullptr;
   float* res = nullptr;  // [B] max QP residual at the last step of the last launch
+  int* work = nullptr;   // work-item counter of a several-job launch led by this state
   int t = 0;
 };
 
@@ -783,12 +784,18 @@ int bodex_state_create(bodex_hand_t h, int B, int s, bodex_state_t* out) {
     }
     cudaMemset(*bufs[k], 0, cnt[k] * sizeof(float));
   }
+  if (cudaMalloc(&S->work, sizeof(int)) != cudaSuccess) {
+    for (int k = 0; k < 6; ++k) cudaFree(*bufs[k]);
+    delete S;
+    return fail(BODEX_ERR_OOM, "cudaMalloc state");
+  }
   *out = S;
   return BODEX_OK;
 }
 
 int bodex_state_destroy(bodex_state_t S) {
   if (!S) return BODEX_OK;
+  cudaFree(S->work);
   cudaFree(S->res);
   cudaFree(S->x);
   cudaFree(S->am);
@@ -937,7 +944,8 @@ int bodex_step_multi(const bodex_job* jobs, int n_jobs, const bodex_step_params*
   std::memset(MA, 0, sizeof(MultiArgs));
   size_t bytes = 0;
   int total = 0, nj = 0;
-  int take[BODEX_MAX_JOBS];
+  int take[BODEX_MAX_JOBS], tiles[BODEX_MAX_JOBS];
+  double cost[BODEX_MAX_JOBS];
   for (int j = 0; j < n_jobs; ++j) {
     const bodex_job& J = jobs[j];
     bodex_state_t S = J.state;
@@ -975,19 +983,47 @@ int bodex_step_multi(const bodex_job* jobs, int n_jobs, const bodex_step_params*
     A.status = J.status;
     A.res = S->res;
     MA->m[nj] = m;
-    MA->cta_begin[nj] = total;
-    total += (S->B + gpb - 1) / gpb;
+    tiles[nj] = (S->B + gpb - 1) / gpb;
+    // cost of one tile: steps x wrenches x (ADMM work per iteration, 26 m + 9 m^2 + ...,
+    // taken as m^2; or m for the exact solve, whose oracle is linear in m)
+    const bool ex = params->qp.solver == BODEX_QP_EXACT;
+    cost[nj] = (double)J.n_steps * J.s * (ex ? m : m * m);
+    total += tiles[nj];
     bytes = std::max(bytes, b);
     take[nj] = j;
     ++nj;
   }
   MA->n_jobs = nj;
-  MA->cta_begin[nj] = total;
+  MA->total = total;
   int r = BODEX_OK;
   if (nj > 0) {
+    // work items job by job: the costliest job's tiles first (stable on
+    // ties) for the pulling schedule, the caller's order otherwise
+    const bool pull = params->work_pulling != 0;
+    int ord[BODEX_MAX_JOBS];
+    for (int k = 0; k < nj; ++k) ord[k] = k;
+    if (pull) std::stable_sort(ord, ord + nj, [&](int a, int b2) { return cost[a] > cost[b2]; });
+    int acc = 0;
+    for (int k = 0; k < nj; ++k) {
+      MA->order_job[k] = ord[k];
+      MA->order_begin[k] = acc;
+      acc += tiles[ord[k]];
+    }
+    MA->order_begin[nj] = acc;
+    // the item counter lives with the first job's state (calls that share a
+    // state are serialised by the caller, so no two launches share it)
+    MA->counter = jobs[take[0]].state->work;
+    cudaStream_t st = as_stream(stream);
+    if (pull) {
+      const cudaError_t e = cudaMemsetAsync(MA->counter, 0, sizeof(int), st);
+      if (e != cudaSuccess) {
+        delete MA;
+        return cuda_fail(e, "cudaMemsetAsync(work counter)");
+      }
+    }
     const bool exact = params->qp.solver == BODEX_QP_EXACT;
     const bool adapt = !exact && params->qp.eps_abs > 0.f && params->qp.adaptive_rho;
-    r = launch_multi(adapt, exact, *MA, total, bytes, as_stream(stream));
+    r = launch_multi(adapt, exact, pull, *MA, bytes, st);
     if (r == BODEX_OK)
       for (int k = 0; k < nj; ++k) jobs[take[k]].state->t += jobs[take[k]].n_steps;
   }

@@ -1099,11 +1099,13 @@ struct ExactQP {
     int kb[M];
 #pragma unroll
     for (int i = 0; i < M; ++i) {
-      float best = gy[3 * i] + c.mu * gy[3 * i + 1];
+      // every multiply-add spelled out: the value must not depend on the
+      // code the solve is inlined into (the compiler's contraction does)
+      float best = fmaf(c.mu, gy[3 * i + 1], gy[3 * i]);
       int k0 = 0;
 #pragma unroll
       for (int k = 1; k < 8; ++k) {
-        const float v = gy[3 * i] + c.mu * fmaf(ck(k), gy[3 * i + 1], sk(k) * gy[3 * i + 2]);
+        const float v = fmaf(c.mu, fmaf(ck(k), gy[3 * i + 1], __fmul_rn(sk(k), gy[3 * i + 2])), gy[3 * i]);
         if (v < best) best = v, k0 = k;
       }
       cb[i] = best;
@@ -1153,7 +1155,7 @@ struct ExactQP {
       const float f = f_of(v, i);
       if (f != 0.f) {
         const int k = (v.code >> (4 * i)) & 7;
-        const float fd = f * c.mu * ck(k), fe = f * c.mu * sk(k);
+        const float fm = __fmul_rn(f, c.mu), fd = __fmul_rn(fm, ck(k)), fe = __fmul_rn(fm, sk(k));
 #pragma unroll
         for (int r = 0; r < 6; ++r)
           q[r] = fmaf(f, G[r * NV + 3 * i], fmaf(fd, G[r * NV + 3 * i + 1], fmaf(fe, G[r * NV + 3 * i + 2], q[r])));
@@ -1163,11 +1165,11 @@ struct ExactQP {
   __device__ static void accumulate_y(const Vtx& v, float w, const AdmmCfg& c, float* y) {
 #pragma unroll
     for (int i = 0; i < M; ++i) {
-      const float f = w * f_of(v, i);
+      const float fo = f_of(v, i), f = __fmul_rn(w, fo), fm = __fmul_rn(f, c.mu);
       const int k = (v.code >> (4 * i)) & 7;
-      y[3 * i] += f;
-      y[3 * i + 1] = fmaf(f * c.mu, ck(k), y[3 * i + 1]);
-      y[3 * i + 2] = fmaf(f * c.mu, sk(k), y[3 * i + 2]);
+      y[3 * i] = fmaf(w, fo, y[3 * i]);
+      y[3 * i + 1] = fmaf(fm, ck(k), y[3 * i + 1]);
+      y[3 * i + 2] = fmaf(fm, sk(k), y[3 * i + 2]);
     }
   }
   // nearest point of the affine hull of P[0..n-1]: weights al (sum 1);
@@ -1372,7 +1374,7 @@ struct ExactQP {
         xq = fmaf(x[r], q[r], xq);
       }
       gap = xx - xq;
-      if (gap <= 1e-5f * xx + 1e-7f || n >= K) break;
+      if (gap <= fmaf(1e-5f, xx, 1e-7f) || n >= K) break;
       // |x| falls at every major step in exact arithmetic; three steps
       // without a relative 1e-6 decrease: float32 resolution is reached
       stall = xx > prev_xx * (1.f - 1e-6f) ? stall + 1 : 0;

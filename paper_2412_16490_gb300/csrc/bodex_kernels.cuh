@@ -1049,31 +1049,33 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
     __syncthreads();
   }
 
-  // ---- write back
-  if (!active) return;
-  if (lane == 0) {
-    if (A.E) A.E[b] = sc[0];
-    if (A.status) A.status[b] = *stat;
-    if (A.res) A.res[b] = sc[2];
-  }
-  if (MODE == MODE_STEP) {
-    for (int k = lane; k < D; k += S) {
-      A.x_state[(size_t)b * D + k] = xs[k];
-      A.am[(size_t)b * D + k] = ams[k];
-      A.av[(size_t)b * D + k] = avs[k];
+  // ---- write back (no early return: the several-job kernel runs this
+  // function once per work item, with barriers between items)
+  if (active) {
+    if (lane == 0) {
+      if (A.E) A.E[b] = sc[0];
+      if (A.status) A.status[b] = *stat;
+      if (A.res) A.res[b] = sc[2];
     }
-  }
-  if (MODE == MODE_EVAL && A.qy && CONE != CONE_EXACT) {
+    if (MODE == MODE_STEP) {
+      for (int k = lane; k < D; k += S) {
+        A.x_state[(size_t)b * D + k] = xs[k];
+        A.am[(size_t)b * D + k] = ams[k];
+        A.av[(size_t)b * D + k] = avs[k];
+      }
+    }
+    if (MODE == MODE_EVAL && A.qy && CONE != CONE_EXACT) {
 #pragma unroll
-    for (int a = 0; a < NV; ++a) A.qy[a * NQ + q] = y[a];
+      for (int a = 0; a < NV; ++a) A.qy[a * NQ + q] = y[a];
 #pragma unroll
-    for (int r = 0; r < NC; ++r) A.qw[r * NQ + q] = w[r];
-  }
-  if (MODE == MODE_EVAL) {
-    if (A.Qout) A.Qout[q] = per[L::oQ + lane];
-    if (A.yout)
+      for (int r = 0; r < NC; ++r) A.qw[r * NQ + q] = w[r];
+    }
+    if (MODE == MODE_EVAL) {
+      if (A.Qout) A.Qout[q] = per[L::oQ + lane];
+      if (A.yout)
 #pragma unroll
-      for (int a = 0; a < NV; ++a) A.yout[q * NV + a] = y[a];
+        for (int a = 0; a < NV; ++a) A.yout[q * NV + a] = y[a];
+    }
   }
 }
 
@@ -1085,32 +1087,66 @@ __global__ void __launch_bounds__(CTA_LANES, CONE == CONE_EXACT ? 2 : 4) fused_k
 
 // ============================================================================ kernel: several jobs in one launch
 // Jobs with different hand templates (m = 3, 4, 5), objects, batch sizes,
-// wrench sets and step counts share one launch: CTA c belongs to the job j
-// with cta_begin[j] <= c < cta_begin[j+1] and runs that job's fused step on
-// its tile of grasps.  The table travels in the kernel parameters, so a
-// launch needs no device memory of its own.
+// wrench sets and step counts share one launch, every job's 200 (or n)
+// upper steps inside it.  A work item is one tile of one job (the grasps of
+// one CTA of that job's own launch).  Two schedules (step_params
+// .work_pulling):
+//   * one CTA per item, items numbered job by job in the caller's order:
+//     the hardware's block scheduler hands them to SMs as slots free up;
+//   * a persistent grid (PULL) of as many CTAs as fit on the GPU at once,
+//     items numbered job by job in decreasing order of cost (steps x
+//     wrenches x ADMM work per iteration, or steps x wrenches x contacts for
+//     the exact solve): each CTA takes the next item from one global counter
+//     (atomicAdd; zeroed by the host on the launch's stream before the
+//     launch) until none is left.  Measured slower on the mixed-template
+//     batch (the item loop costs the step registers: 488 bytes of spills at
+//     the 168-register cap), so it is not the default.
+// The job table travels in the kernel parameters.
 struct MultiArgs {
   int n_jobs;
+  int total;                            // work items
+  int* counter;                         // next work item (device, zeroed before the launch)
   int m[BODEX_MAX_JOBS];
-  int cta_begin[BODEX_MAX_JOBS + 1];
+  int order_job[BODEX_MAX_JOBS];        // jobs in decreasing cost
+  int order_begin[BODEX_MAX_JOBS + 1];  // first item of the k-th job in that order
   FusedArgs job[BODEX_MAX_JOBS];
 };
 
 static_assert(sizeof(MultiArgs) <= 32000, "job table must fit in the kernel parameter space");
 
-template <bool ADAPT, bool EXACT = false>
-__global__ void __launch_bounds__(CTA_LANES, EXACT ? 2 : 4) multi_kernel(const __grid_constant__ MultiArgs A) {
-  extern __shared__ __align__(16) float smem[];
+// Work item w: the k-th job in the item order, the tile w - order_begin[k].
+template <bool ADAPT, bool EXACT>
+__device__ __forceinline__ void multi_item(const MultiArgs& A, int w, float* smem) {
   constexpr int CN = EXACT ? CONE_EXACT : CONE_ANY;
-  const int c = blockIdx.x;
-  int j = 0;
-  while (j + 1 < A.n_jobs && c >= A.cta_begin[j + 1]) ++j;
+  int k = 0;
+  while (k + 1 < A.n_jobs && w >= A.order_begin[k + 1]) ++k;
+  const int j = A.order_job[k];
   const FusedArgs& J = A.job[j];
-  const int cta = c - A.cta_begin[j];
+  const int cta = w - A.order_begin[k];
   switch (A.m[j]) {
     case 3: fused_cta<3, MODE_STEP, CN, ADAPT>(J, cta, J.gpb, smem); break;
     case 4: fused_cta<4, MODE_STEP, CN, ADAPT>(J, cta, J.gpb, smem); break;
     default: fused_cta<5, MODE_STEP, CN, ADAPT>(J, cta, J.gpb, smem); break;
+  }
+}
+
+template <bool ADAPT, bool EXACT = false, bool PULL = false>
+__global__ void __launch_bounds__(CTA_LANES, EXACT ? 2 : 4) multi_kernel(const __grid_constant__ MultiArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  if constexpr (!PULL) {
+    multi_item<ADAPT, EXACT>(A, (int)blockIdx.x, smem);  // one item per CTA, no loop
+  } else {
+    __shared__ int item;
+#pragma unroll 1
+    for (;;) {
+      if (threadIdx.x == 0) item = atomicAdd(A.counter, 1);
+      __syncthreads();
+      const int w = item;
+      __syncthreads();  // every thread has read the item before thread 0 takes the next
+      if (w >= A.total) break;
+      multi_item<ADAPT, EXACT>(A, w, smem);
+      __syncthreads();  // shared memory is free for the next item
+    }
   }
 }
 
@@ -1240,4 +1276,4 @@ int launch_fused_m4(int mode, const FusedArgs& A, cudaStream_t st);
 int launch_fused_m5(int mode, const FusedArgs& A, cudaStream_t st);
 int launch_qp(int m, const float* G, int B, const float* T, int s, const AdmmCfg& cfg, int warm, float* y, float* z,
               float* lam, float* Q, int32_t* iters, int32_t* status, float* res, cudaStream_t st);
-int launch_multi(bool adapt, bool exact, const MultiArgs& MA, int total, size_t bytes, cudaStream_t st);
+int launch_multi(bool adapt, bool exact, bool pull, const MultiArgs& MA, size_t bytes, cudaStream_t st);

@@ -179,14 +179,19 @@ typedef struct bodex_qp_params {
                         start reads lam with params->rho.  Results are unchanged up to
                         the residual target; 0: fixed rho.  Ignored when eps_abs == 0
                         (fixed iteration counts). */
-  int polish;        /* 1 (pyramid cone, eps_reg = 0): after the ADMM run, solve every QP
-                        exactly in FP64 by Wolfe's minimum-norm-point method (the QP is
-                        the nearest point of the wrench polytope G C to beta t; Wolfe 1976)
-                        and replace y and Q by that minimiser and optimum (Q to FP64
-                        rounding, y rounded to float).  Such QPs carry BODEX_ST_POLISHED
-                        and not BODEX_ST_NOT_CONVERGED; z, lam, res and iters stay those of
-                        the ADMM run.  A QP the exact solve gives up on (200 oracle calls)
-                        keeps its ADMM result.  0: off.  bodex_qp_solve_batch only. */
+  int polish;        /* pyramid cone, eps_reg = 0; bodex_qp_solve_batch only.
+                        1: after the ADMM run, solve every QP exactly in FP64 by Wolfe's
+                        minimum-norm-point method (the QP is the nearest point of the
+                        wrench polytope G C to beta t; Wolfe 1976) and replace y and Q by
+                        that minimiser and optimum (Q to FP64 rounding, y rounded to
+                        float).  2 (with eps_abs > 0 and a status array): solve exactly,
+                        by the float32 method of BODEX_QP_EXACT, only the QPs that ADMM
+                        left above eps_abs after max_iter iterations; the others keep
+                        their ADMM results bit for bit.  A replaced QP carries
+                        BODEX_ST_POLISHED and not BODEX_ST_NOT_CONVERGED; z, lam, res and
+                        iters stay those of the ADMM run.  A QP the exact solve gives up
+                        on (200 oracle calls in FP64, 64 in float32) keeps its ADMM
+                        result.  0: off. */
   int solver;        /* lower-level method.  BODEX_QP_ADMM: the OSQP-form ADMM above.
                         BODEX_QP_EXACT (pyramid cone, eps_reg = 0): the exact optimum by
                         Wolfe's minimum-norm-point method in float32, one QP per thread

@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(RF_LANES * RF_GPB) refine_kernel(RefineArgs A)
     __syncthreads();
     if (active) {
       const int tstep = A.t0 + step + 1;
-      const float c1 = 1.f - powf(A.b1, (float)tstep), c2 = 1.f - powf(A.b2, (float)tstep);
+      const float c1 = 1.f - exp2f((float)tstep * log2f(A.b1)), c2 = 1.f - exp2f((float)tstep * log2f(A.b2));
       if (lane == 0 && A.E) {
         float e = 0.f;
         for (int i = 0; i < M; ++i) e += Ei[i];
@@ -363,6 +363,7 @@ int check_qp_params(const bodex_qp_params* p, int m) {
     return fail(BODEX_ERR_INVALID, "cone must be BODEX_CONE_PYRAMID or BODEX_CONE_ELLIPTIC");
   if (p->solver != BODEX_QP_ADMM && p->solver != BODEX_QP_EXACT)
     return fail(BODEX_ERR_INVALID, "solver must be BODEX_QP_ADMM or BODEX_QP_EXACT");
+  if (p->polish < 0 || p->polish > 2) return fail(BODEX_ERR_INVALID, "polish must be 0, 1 or 2");
   if (p->solver == BODEX_QP_EXACT && (p->cone != BODEX_CONE_PYRAMID || p->eps_reg != 0.f || p->max_iter < 1))
     return fail(BODEX_ERR_INVALID, "the exact solver needs the pyramid cone, eps_reg = 0 and max_iter >= 1");
   return BODEX_OK;

@@ -1581,11 +1581,12 @@ __device__ __forceinline__ float proj_row_soc(const float* w, int row, float gam
 
 // Runs ADMM on one QP until both residuals are <= eps (checked every
 // `check` iterations, eps > 0) or `iters` iterations.  Returns the count
-// used; rp/rd receive the last residuals (computed once at the end when
-// eps == 0).
+// used; rp/rd receive the last residuals (with eps == 0, computed once at
+// the end, and only when want_res: the fused step reports them for its
+// last upper step alone).
 template <int M, int CONE>
 __device__ inline int admm_solve(float* y, float* w, const float* mq, const float* Kinv, const float* G,
-                                 const AdmmCfg& c, float& rp, float& rd, bool& conv) {
+                                 const AdmmCfg& c, float& rp, float& rd, bool& conv, bool want_res = true) {
   auto iterate = [&]() {
     if (CONE == CONE_SOC) admm_iteration_soc<M>(y, w, mq, Kinv, c, c.rho);
     else admm_iteration<M>(y, w, mq, Kinv, c, c.rho);
@@ -1613,7 +1614,7 @@ __device__ inline int admm_solve(float* y, float* w, const float* mq, const floa
   } else {
 #pragma unroll 1
     for (; it < c.iters; ++it) iterate();
-    residuals();
+    if (want_res) residuals();
   }
   return it;
 }

@@ -623,6 +623,57 @@ __global__ void __launch_bounds__(128) qp_exact_kernel(const float* __restrict__
   if (status_out) status_out[q] = st;
 }
 
+// ============================================================================ kernel: exact finish of the ADMM stragglers
+// qp.polish = 2: after the ADMM kernel, the QPs it left above the residual
+// target (BODEX_ST_NOT_CONVERGED) are solved exactly by the float32
+// minimum-norm-point method (ExactQP).  A block takes a range of
+// QP_FINISH_RANGE consecutive QPs, gathers the flagged ones into shared
+// memory (ballot and prefix count), and its threads solve them one each.
+// A finished QP takes the exact y and Q, gets BODEX_ST_POLISHED and loses
+// BODEX_ST_NOT_CONVERGED; its z, lam, residuals and iteration count stay
+// those of the ADMM run.  The QPs ADMM converged are not touched.
+constexpr int QP_FINISH_RANGE = 256, QP_FINISH_THREADS = 128;
+
+template <int M>
+__global__ void __launch_bounds__(QP_FINISH_THREADS) qp_finish_kernel(const float* __restrict__ Gin, int B,
+                                                                      const float* __restrict__ T, int S,
+                                                                      AdmmCfg cfg, float* y_io, float* Qout,
+                                                                      int32_t* status_io) {
+  constexpr int NV = 3 * M;
+  __shared__ int list[QP_FINISH_RANGE];
+  __shared__ int count;
+  const size_t n = (size_t)B * S, q0 = (size_t)blockIdx.x * QP_FINISH_RANGE;
+  if (threadIdx.x == 0) count = 0;
+  __syncthreads();
+  for (int k = threadIdx.x; k < QP_FINISH_RANGE; k += blockDim.x) {
+    const size_t q = q0 + k;
+    const bool flag = q < n && (status_io[q] & BODEX_ST_NOT_CONVERGED) && !(status_io[q] & BODEX_ST_NONFINITE);
+    const unsigned bal = __ballot_sync(0xffffffffu, flag);
+    int base = 0;
+    if ((threadIdx.x & 31) == 0 && bal) base = atomicAdd(&count, __popc(bal));
+    base = __shfl_sync(0xffffffffu, base, 0);
+    if (flag) list[base + __popc(bal & ((1u << (threadIdx.x & 31)) - 1u))] = k;
+  }
+  __syncthreads();
+  const int cnt = count;
+  for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+    const size_t q = q0 + list[i];
+    const size_t b = q / S;
+    const int j = (int)(q % S);
+    const float* G = Gin + b * 6 * NV;
+    float t[6], y[NV], Q, gap;
+#pragma unroll
+    for (int r = 0; r < 6; ++r) t[r] = T[j * 6 + r];
+    typename ExactQP<M>::Corral C;
+    C.n = 0;
+    if (ExactQP<M>::solve(G, t, cfg, 64, C, y, Q, gap) < 0) continue;
+#pragma unroll
+    for (int a = 0; a < NV; ++a) y_io[q * NV + a] = y[a];
+    Qout[q] = Q;
+    status_io[q] = (status_io[q] & ~BODEX_ST_NOT_CONVERGED) | BODEX_ST_POLISHED;
+  }
+}
+
 // ============================================================================ kernel: solution polishing
 // A pass after qp_solve_kernel when qp.polish is set (pyramid QPs with
 // eps_reg = 0): one thread per QP solves the QP exactly in FP64 by the
@@ -767,6 +818,7 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
     for (int r = 0; r < 6; ++r) t[r] = A.T[lane * 6 + r];
   __syncthreads();
 
+  const float lb1 = log2f(A.b1), lb2 = log2f(A.b2);
   for (int step = 0; step < A.n_steps; ++step) {
     // ---- A1-A3: kinematics, nearest-point query, grasp matrix (lane = contact)
     if (active && lane < M) {
@@ -910,8 +962,9 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
         float mq[NV];
         neg_q<M>(Gs, t, cfg.beta, mq);
         float rp, rd;
-        if (soc) admm_solve<M, CONE_SOC>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
-        else admm_solve<M, CONE_PYR>(y, w, mq, kin, Gs, cfg, rp, rd, conv);
+        const bool last = step == A.n_steps - 1;
+        if (soc) admm_solve<M, CONE_SOC>(y, w, mq, kin, Gs, cfg, rp, rd, conv, last);
+        else admm_solve<M, CONE_PYR>(y, w, mq, kin, Gs, cfg, rp, rd, conv, last);
         if (step == A.n_steps - 1) atomicMax(reinterpret_cast<int*>(sc + 2), __float_as_int(fmaxf(rp, rd)));
       }
       finish_qp();
@@ -1021,7 +1074,9 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
     if (active) {
       const float* cb = per + L::oCB;
       const int tstep = A.t0 + step + 1;
-      const float c1 = 1.f - powf(A.b1, (float)tstep), c2 = 1.f - powf(A.b2, (float)tstep);
+      // bias corrections 1 - b^t as 1 - 2^(t log2 b): a function of t alone,
+      // so a run split over several launches gives the same values
+      const float c1 = 1.f - exp2f((float)tstep * lb1), c2 = 1.f - exp2f((float)tstep * lb2);
       for (int k = lane; k < D; k += S) {
         float g = 0.f;
         if (k < 6) {
@@ -1260,10 +1315,16 @@ inline int run_qp(const float* G, int B, const float* T, int s, const AdmmCfg& c
     qp_solve_kernel<M, CONE_PYR><<<(B + gpb - 1) / gpb, gpb * s, bytes, st>>>(G, B, T, s, cfg, warm, y, z, lam, Q,
                                                                               iters, status, res);
     if (int r = launch_err("qp_solve_kernel launch")) return r;
-    if (cfg.polish && cfg.eps_reg == 0.f) {
+    if (cfg.polish == 1 && cfg.eps_reg == 0.f) {
       const size_t n = (size_t)B * s;
       qp_polish_kernel<M><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(G, B, T, s, cfg, y, Q, status);
       return launch_err("qp_polish_kernel launch");
+    }
+    if (cfg.polish == 2 && cfg.eps_reg == 0.f && cfg.eps > 0.f && status) {
+      const size_t n = (size_t)B * s;
+      qp_finish_kernel<M><<<(unsigned)((n + QP_FINISH_RANGE - 1) / QP_FINISH_RANGE), QP_FINISH_THREADS, 0, st>>>(
+          G, B, T, s, cfg, y, Q, status);
+      return launch_err("qp_finish_kernel launch");
     }
     return BODEX_OK;
   }

@@ -84,6 +84,35 @@ def test_fullsize_qp_batch_sampled(full):
     assert (d >= lo - tol).all() and (d <= hi + tol).all()
 
 
+def test_fullsize_qp_batch_admm_then_exact_finish(full):
+    """qp.polish = 2 on the bench's QP batch: ADMM to 1e-5 with a cap of 1000
+    iterations, then the exact float32 solve of the QPs it left unconverged.
+    Every QP ends converged or exactly solved; the converged ones are bit for
+    bit those of the same ADMM run without the finish; the finished ones of
+    the sampled grasps are within 1e-4 |Q*| + 1e-6 of the oracle's."""
+    hand, obj, x0, T, P, H, Ob = full
+    G = bx.bodex_fk_contacts(H, Ob, cuda(x0))["G"]
+    prm = bx.qp_params(mu=MU, beta=BETA, gamma=GAMMA, eps_abs=1e-5, max_iter=1000, check_every=10, polish=2)
+    out = bx.bodex_qp_solve_batch(G, cuda(T), prm)
+    prm.polish = 0
+    adm = bx.bodex_qp_solve_batch(G, cuda(T), prm)
+    st, st0 = host(out["status"]), host(adm["status"])
+    assert ((st & bx.ST_NOT_CONVERGED) == 0).all()
+    fin = (st & bx.ST_POLISHED) != 0
+    assert (fin == ((st0 & bx.ST_NOT_CONVERGED) != 0)).all()  # exactly the stragglers were finished
+    assert 0 < fin.mean() < 0.5
+    y, y0 = host(out["y"]), host(adm["y"])
+    assert np.array_equal(y[~fin], y0[~fin]) and np.array_equal(host(out["Q"])[~fin], host(adm["Q"])[~fin])
+    Gs = host(G)[SAMPLE].astype(np.float64)
+    ref = O.qp_solve(Gs, T, mu=MU, beta=BETA, gamma=GAMMA)
+    ys = y[SAMPLE].astype(np.float64)
+    Qy = ((BETA * T[None].astype(np.float64) - np.einsum("bri,bsi->bsr", Gs, ys)) ** 2).sum(-1)
+    bar = 1e-4 * np.abs(ref["Q"]) + 1e-6
+    fs = fin[SAMPLE]
+    assert fs.sum() >= 10
+    assert (np.abs(Qy - ref["Q"])[fs] <= bar[fs]).all()
+
+
 def test_fullsize_qp_batch_exact_solver(full):
     """The same 49,152 QPs with qp.solver = EXACT: no QP stopped by the cap,
     and the sampled grasps' values within 1e-4 |Q*| + 1e-6 of the oracle's."""

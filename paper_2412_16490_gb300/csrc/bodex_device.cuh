@@ -640,12 +640,21 @@ __device__ __forceinline__ float proj_row(float w, int row, float gamma) {
 
 // Contribution of one contact's nine rows (v0: the f_n row, vk: the facets)
 // to A^T v.  The sum row's entry is added to the normal component by the caller.
+// Facets k and k+4 have opposite (d, e) normals (cos, sin of (2k+1) pi/8:
+// (C8, S8), (S8, C8), (-S8, C8), (-C8, S8) for k = 0..3), and facets 0, 7
+// (1, 6; 2, 5; 3, 4) are mirror images across d: with the pair sums
+// s_07 = v_0 + v_7, ... and differences d_07 = v_0 - v_7, ...
+//   sum v = (s_07 + s_34) + (s_16 + s_25),
+//   d: C8 (s_07 - s_34) + S8 (s_16 - s_25),
+//   e: S8 (d_07 + d_34) + C8 (d_16 + d_25)   (d_34 = v_3 - v_4, d_25 = v_2 - v_5).
 __device__ __forceinline__ void At_contact(float v0, const float (&vk)[8], float mu_c8, float& gn, float& gd,
                                            float& ge) {
-  const float sum = ((vk[0] + vk[1]) + (vk[2] + vk[3])) + ((vk[4] + vk[5]) + (vk[6] + vk[7]));
+  const float s07 = vk[0] + vk[7], s34 = vk[3] + vk[4], s16 = vk[1] + vk[6], s25 = vk[2] + vk[5];
+  const float d07 = vk[0] - vk[7], d34 = vk[3] - vk[4], d16 = vk[1] - vk[6], d25 = vk[2] - vk[5];
+  const float sum = (s07 + s34) + (s16 + s25);
   gn = fmaf(-mu_c8, sum, v0);
-  gd = fmaf(C8, (vk[0] + vk[7]) - (vk[3] + vk[4]), S8 * ((vk[1] + vk[6]) - (vk[2] + vk[5])));
-  ge = fmaf(S8, (vk[0] + vk[3]) - (vk[4] + vk[7]), C8 * ((vk[1] + vk[2]) - (vk[5] + vk[6])));
+  gd = fmaf(C8, s07 - s34, S8 * (s16 - s25));
+  ge = fmaf(S8, d07 + d34, C8 * (d16 + d25));
 }
 
 // Per-contact pieces of one ADMM iteration.  admm_iteration and the
@@ -1173,27 +1182,26 @@ struct ExactQP {
     }
   }
   // nearest point of the affine hull of P[0..n-1]: weights al (sum 1);
-  // false when the differences are (numerically) dependent
+  // false when the differences are (numerically) dependent.  The loops over
+  // the working set run to n, not unrolled to K: the unrolled form missed the
+  // instruction cache in the fused step (17% slower there, the same alone)
   __device__ static bool affine_min(const float (&P)[K][6], int n, float (&al)[K]) {
     float U[K - 1][6], R[K - 1][K - 1], sc = 1.f;
+#pragma unroll 1
+    for (int i = 0; i < n; ++i)
 #pragma unroll
-    for (int i = 0; i < K; ++i)
-      if (i < n)
-#pragma unroll
-        for (int r = 0; r < 6; ++r) sc = fmaxf(sc, fabsf(P[i][r]));
-#pragma unroll
-    for (int j = 0; j < K - 1; ++j) {
-      if (j + 1 >= n) break;
+      for (int r = 0; r < 6; ++r) sc = fmaxf(sc, fabsf(P[i][r]));
+#pragma unroll 1
+    for (int j = 0; j + 1 < n; ++j) {
       float u[6];
 #pragma unroll
       for (int r = 0; r < 6; ++r) u[r] = P[j + 1][r] - P[0][r];
-#pragma unroll
-      for (int i = 0; i < K - 1; ++i) R[i][j] = 0.f;
+#pragma unroll 1
+      for (int i = 0; i < j; ++i) R[i][j] = 0.f;
 #pragma unroll
       for (int pass = 0; pass < 2; ++pass)
-#pragma unroll
-        for (int i = 0; i < K - 1; ++i) {
-          if (i >= j) break;
+#pragma unroll 1
+        for (int i = 0; i < j; ++i) {
           float d = 0.f;
 #pragma unroll
           for (int r = 0; r < 6; ++r) d = fmaf(U[i][r], u[r], d);
@@ -1211,32 +1219,25 @@ struct ExactQP {
 #pragma unroll
       for (int r = 0; r < 6; ++r) U[j][r] = u[r] * inv;
     }
-    // alpha' = -R^-1 U^T p_0, alpha_0 = 1 - sum alpha'
     float a1[K - 1];
-#pragma unroll
-    for (int j = K - 2; j >= 0; --j) {
-      if (j + 1 >= n) {
-        a1[j] = 0.f;
-        continue;
-      }
+#pragma unroll 1
+    for (int j = n - 2; j >= 0; --j) {
       float s = 0.f;
 #pragma unroll
       for (int r = 0; r < 6; ++r) s = fmaf(-U[j][r], P[0][r], s);
-#pragma unroll
-      for (int k = K - 2; k > j; --k)
-        if (k + 1 < n) s = fmaf(-R[j][k], a1[k], s);
+#pragma unroll 1
+      for (int k = n - 2; k > j; --k) s = fmaf(-R[j][k], a1[k], s);
       a1[j] = s / R[j][j];
     }
     float a0 = 1.f;
-#pragma unroll
-    for (int j = 0; j < K - 1; ++j) {
+#pragma unroll 1
+    for (int j = 0; j + 1 < n; ++j) {
       al[j + 1] = a1[j];
       a0 -= a1[j];
     }
     al[0] = a0;
     return true;
   }
-
   // The working set ("corral"): n points with their vertex codes and weights.
   struct Corral {
     int n;

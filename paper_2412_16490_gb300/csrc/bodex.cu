@@ -749,6 +749,7 @@ int bodex_qp_solve_batch(const float* G, int B, int m, const float* T, int s, co
   if (B > 0 && (!G || !T || !y || !z || !lam || !Q)) return fail(BODEX_ERR_INVALID, "null array");
   if (int r = check_qp_params(params, m)) return r;
   if (params->strict && !status) return fail(BODEX_ERR_INVALID, "strict mode needs a status array");
+  if (params->polish == 2 && !status) return fail(BODEX_ERR_INVALID, "polish = 2 needs a status array");
   AdmmCfg cfg = admm_cfg(*params);
   // K^-1 in FP64 for any residual target: an FP32 K^-1 raises the ADMM floor
   // (on the paper batch 98.2% instead of 99.5% of the QPs reach 1e-5)

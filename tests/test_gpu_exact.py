@@ -112,3 +112,41 @@ def test_exact_several_job_launch_equals_single_launches():
     bx.bodex_step_multi(multi, sp)
     for a, b in zip(single, multi):
         assert torch.equal(a["state"].pose(), b["state"].pose())
+
+
+@pytest.mark.parametrize("m,s,B", [(3, 12, 21), (4, 6, 50), (5, 1, 7), (4, 16, 9), (5, 12, 1)])
+def test_exact_qp_shapes_match_oracle(m, s, B):
+    """The standalone exact solver over hand sizes, wrench counts from 1 to
+    16 and ragged batches (B not a multiple of a block's grasps)."""
+    T = I.wrench_set(12)[:s] if s <= 12 else np.concatenate([I.wrench_set(12), I.wrench_set(6)[:4]])
+    p, n = I.random_contacts(B, m, seed=60 + m + s)
+    G32 = O.grasp_matrix(p, n).astype(np.float32)
+    ref = O.qp_solve(G32.astype(np.float64), T)
+    out = bx.bodex_qp_solve_batch(cuda(G32), cuda(T), bx.qp_params(max_iter=64, solver=bx.QP_EXACT))
+    assert (host(out["status"]) == 0).all()
+    assert (np.abs(host(out["Q"]) - ref["Q"]) <= 1e-4 * np.abs(ref["Q"]) + 1e-6).all()
+
+
+def test_admm_then_exact_finish_small_batch():
+    """qp.polish = 2 on a ragged batch: every QP converged by ADMM or exactly
+    finished, the finished ones within the QP-value bar; without a status
+    array the call is refused."""
+    T = I.wrench_set(12)
+    p, n = I.random_contacts(37, 5, seed=77)
+    G32 = O.grasp_matrix(p, n).astype(np.float32)
+    ref = O.qp_solve(G32.astype(np.float64), T)
+    prm = bx.qp_params(eps_abs=1e-5, max_iter=150, check_every=10, polish=2)
+    out = bx.bodex_qp_solve_batch(cuda(G32), cuda(T), prm)
+    st = host(out["status"])
+    assert ((st & bx.ST_NOT_CONVERGED) == 0).all()
+    fin = (st & bx.ST_POLISHED) != 0
+    assert fin.any()
+    assert (np.abs(host(out["Q"]) - ref["Q"])[fin] <= (1e-4 * np.abs(ref["Q"]) + 1e-6)[fin]).all()
+    import ctypes as C
+    L = bx.load()
+    Gd, Td = cuda(G32), cuda(T)
+    y, z, lam, Q = (torch.zeros(sh, device="cuda") for sh in ((37, 12, 15), (37, 12, 46), (37, 12, 46), (37, 12)))
+    ptr = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+    rc = L.bodex_qp_solve_batch(ptr(Gd), 37, 5, ptr(Td), 12, C.byref(prm), ptr(y), ptr(z), ptr(lam), ptr(Q), None, None,
+                                None, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert rc == 1

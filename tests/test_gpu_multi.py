@@ -105,3 +105,24 @@ def test_work_pulling_launch_equals_single_launches(solver):
         else:
             np.testing.assert_allclose(host(j["pull"].pose()), host(j["alone"].pose()), rtol=0, atol=1e-5)
         assert torch.equal(j["once"].pose(), j["alone"].pose()), j["tpl"].name
+
+
+@pytest.mark.parametrize("wp", [0, 1])
+def test_several_job_launch_with_empty_and_idle_jobs(wp):
+    """Jobs with no grasps or no steps are skipped in both schedules; the
+    others get their own launch's result; a launch of no jobs is a no-op."""
+    T = cuda(I.wrench_set(12))
+    sp = bx.step_params(I.default_params(), qp=bx.qp_params(max_iter=20), work_pulling=wp)
+    hand = I.hand_template("hand5")
+    H, Ob = bx.Hand(hand), bx.Object(I.grid_object(2))
+    x0 = I.initial_poses(hand, I.grid_object(2), 19, seed=3)
+    empty, idle, real, alone = bx.State(H, 0, 12), bx.State(H, 19, 12), bx.State(H, 19, 12), bx.State(H, 19, 12)
+    for st in (idle, real, alone):
+        st.set_pose(cuda(x0))
+    bx.bodex_step_multi([dict(hand=H, obj=Ob, state=empty, T=T, n_steps=5),
+                         dict(hand=H, obj=Ob, state=idle, T=T, n_steps=0),
+                         dict(hand=H, obj=Ob, state=real, T=T, n_steps=5)], sp)
+    bx.bodex_step(H, Ob, alone, T, 5, sp)
+    assert torch.equal(real.pose(), alone.pose())
+    assert torch.equal(idle.pose(), cuda(x0)) and idle.adam()[2] == 0
+    bx.bodex_step_multi([], sp)

@@ -30,7 +30,7 @@ struct HandDev {
   int n, m, D, S;
   float alpha;
   int parent[MAXJ];
-  float offset[MAXJ][12];
+  alignas(16) float offset[MAXJ][12];  // rows [R_r0 R_r1 R_r2 t_r], one float4 each
   float axis[MAXJ][3];
   float qmin[MAXD], qmax[MAXD];
   int clink[MAXM];
@@ -186,9 +186,9 @@ __device__ inline void fk_link(const HandDev& H, int i, const float* x, Tf& T, f
     Tf off;
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-#pragma unroll
-      for (int cc = 0; cc < 3; ++cc) off.R[3 * r + cc] = H.offset[j][4 * r + cc];
-      off.t[r] = H.offset[j][4 * r + 3];
+      const float4 o = reinterpret_cast<const float4*>(H.offset[j])[r];
+      off.R[3 * r] = o.x, off.R[3 * r + 1] = o.y, off.R[3 * r + 2] = o.z;
+      off.t[r] = o.w;
     }
     Tf base;
     tf_mul(T, off, base);
@@ -446,14 +446,9 @@ __device__ __forceinline__ double fma_r(double a, double b, double c) { return f
 template <int M, typename R>
 __device__ inline R woodbury_M_entry(const float* G, int e, const AdmmCfg& c, R idn, R idt) {
   constexpr int NV = 3 * M;
-  int a = 0, b = 0, k = e;
-  for (a = 0; a < 7; ++a) {
-    if (k < 7 - a) {
-      b = a + k;
-      break;
-    }
-    k -= 7 - a;
-  }
+  // rows of the 7 x 7 upper triangle start at entries 0, 7, 13, 18, 22, 25, 27
+  const int a = (e >= 7) + (e >= 13) + (e >= 18) + (e >= 22) + (e >= 25) + (e >= 27);
+  const int b = e - (a * 7 - (a * (a - 1)) / 2) + a;
   if (b < 6) {  // both columns from sqrt2 G^T: normal and tangential parts summed apart
     R sn = 0, st = 0;
 #pragma unroll
@@ -507,7 +502,7 @@ __device__ __forceinline__ void load_u_row(const R* Us, int i, R (&u)[7]) {
 template <int M, typename R>
 __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const float* G, float* scratch, float* Kinv,
                                            const AdmmCfg& c) {
-  constexpr int NV = 3 * M, NTRI = Admm<M>::NTRI;
+  constexpr int NV = 3 * M;
   const DiagK dk = diag_k(c);
   R* Ms = reinterpret_cast<R*>(scratch);  // 28
   R* Us = Ms + 28;                        // NV rows of 8
@@ -524,16 +519,31 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
   R L[28];
   R ild[7];  // reciprocals of the diagonal of L
   auto factor = [&]() {
+    if constexpr (sizeof(R) == 4) {  // seven 16-byte loads (the scratch is 16-byte aligned)
 #pragma unroll
-    for (int e = 0; e < 28; ++e) L[e] = Ms[e];
+      for (int e = 0; e < 28; e += 4) {
+        const float4 v = *reinterpret_cast<const float4*>(Ms + e);
+        L[e] = v.x, L[e + 1] = v.y, L[e + 2] = v.z, L[e + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 28; ++e) L[e] = Ms[e];
+    }
 #pragma unroll
     for (int j = 0; j < 7; ++j) {
       R d = L[idx(j, j)];
 #pragma unroll
       for (int k = 0; k < j; ++k) d = fma_r(-L[idx(k, j)], L[idx(k, j)], d);
-      const R ljj = sqrt(d > R(1e-30) ? d : R(1e-30));
-      L[idx(j, j)] = ljj;
-      const R il = R(1) / ljj;
+      const R dd = d > R(1e-30) ? d : R(1e-30);
+      R il;
+      if constexpr (sizeof(R) == 4) {  // one reciprocal square root; only 1 / l_jj is used below
+        il = rsqrtf(dd);
+        L[idx(j, j)] = dd * il;
+      } else {
+        const R ljj = sqrt(dd);
+        L[idx(j, j)] = ljj;
+        il = R(1) / ljj;
+      }
       ild[j] = il;
 #pragma unroll
       for (int i = j + 1; i < 7; ++i) {
@@ -583,22 +593,34 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
     }
   }
   __syncthreads();
-  // alpha K^-1 = alpha (Dg^-1 - U U^T): the NTRI packed entries spread evenly
-  // over the grasp's lanes (entry t = (i, j) of the row-major upper triangle)
+  // alpha K^-1 = alpha (Dg^-1 - U U^T), entry (i, j) of the upper triangle
+  // at Admm<M>::tri(i, j).  Lane p takes the columns j1 = p and
+  // j2 = nv-1-p (nv + 1 entries between them, so the lanes' shares are
+  // equal), holds their rows of U in registers and walks i = 0 .. j2 in step
+  // with the grasp's other lanes: at each i they all read the same row of U,
+  // one broadcast load, where spreading single entries over the lanes had
+  // each lane read two rows of its own per entry.
   if (active) {
-    int i = 0, j = lane;  // entry `lane`, then every S-th
-    while (i < NV && j >= NV) j -= NV - 1 - i++;
-    for (int t = lane; t < NTRI; t += S) {
-      R ui[7], uj[7];
-      load_u_row(Us, i, ui);
-      load_u_row(Us, j, uj);
-      R acc = 0;
+    for (int p = lane; p < (NV + 1) / 2; p += S) {
+      const int j1 = p, j2 = NV - 1 - p;
+      R u1[7], u2[7];
+      load_u_row(Us, j1, u1);
+      load_u_row(Us, j2, u2);
+      for (int i = 0; i <= j2; ++i) {
+        R ui[7];
+        load_u_row(Us, i, ui);
+        const R di = (i % 3 == 0) ? idn : idt;
+        R acc = 0;
 #pragma unroll
-      for (int a = 0; a < 7; ++a) acc = fma_r(ui[a], uj[a], acc);
-      const R dg = i == j ? ((i % 3 == 0) ? idn : idt) : R(0);
-      Kinv[t] = (float)(R(c.alpha) * (dg - acc));
-      j += S;  // advance to entry t + S
-      while (i < NV && j >= NV) j -= NV - 1 - i++;
+        for (int a = 0; a < 7; ++a) acc = fma_r(ui[a], u2[a], acc);
+        Kinv[Admm<M>::tri(i, j2)] = (float)(R(c.alpha) * ((i == j2 ? di : R(0)) - acc));
+        if (i <= j1 && j1 < j2) {
+          R acc1 = 0;
+#pragma unroll
+          for (int a = 0; a < 7; ++a) acc1 = fma_r(ui[a], u1[a], acc1);
+          Kinv[Admm<M>::tri(i, j1)] = (float)(R(c.alpha) * ((i == j1 ? di : R(0)) - acc1));
+        }
+      }
     }
   }
   __syncthreads();

@@ -43,8 +43,11 @@ struct Lay {
   static constexpr int oG = 0;
   static constexpr int oK = align4(oG + 6 * NV);  // K^-1 setup scratch (16-byte aligned)
   static constexpr int oCT = oK + WoodburyScratch<M, double>::floats;
+  // per-lane record of the QP outputs: r_j (6), two pad words, then y_j
+  // from a 16-byte boundary (read as float4s by the dE/dG reduction)
+  static constexpr int RYW = 8 + NVP;
   static constexpr int oRY = oCT + CTW * M;
-  static constexpr int oQ = oRY + SMAX * (6 + NV);
+  static constexpr int oQ = oRY + SMAX * RYW;
   static constexpr int oDG = oQ + SMAX;
   static constexpr int oCB = oDG + 6 * NV;
   static constexpr int oX = oCB + M * (6 + MAXCHAIN);
@@ -56,7 +59,7 @@ struct Lay {
   // collision scratch: link frames in the K^-1 setup scratch, sphere centres
   // and slot sums in the r / Q / dE/dG block (both dead before A4)
   static constexpr int COLL_FR = WoodburyScratch<M, double>::floats;
-  static constexpr int COLL_CS = SMAX * (6 + NV) + SMAX + 6 * NV;
+  static constexpr int COLL_CS = SMAX * RYW + SMAX + 6 * NV;
   // per-grasp stride == 12 (mod 32) words: the two or three grasps that
   // share a warp then map the same offset to different banks
   static constexpr int PER = align4(oSC + 4) + ((12 - align4(oSC + 4) % 32) + 32) % 32;
@@ -854,7 +857,7 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
     bool conv = true;
     // r_j, Q_j, the stored iterate and the status of this lane's QP
     auto finish_qp = [&]() {
-      float* ry = per + L::oRY + lane * (6 + NV);
+      float* ry = per + L::oRY + lane * L::RYW;
       float Q = 0.f;
 #pragma unroll
       for (int r = 0; r < 6; ++r) {
@@ -866,7 +869,7 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
       }
 #pragma unroll
       for (int a = 0; a < NV; ++a) {
-        ry[6 + a] = y[a];
+        ry[8 + a] = y[a];
         Q = fmaf(cfg.eps_reg * y[a], y[a], Q);  // regularised value when eps_reg > 0
       }
       per[L::oQ + lane] = Q;
@@ -1005,19 +1008,37 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
       }
     }
     if (active && !A.dfc) {
+      // a lane's task: row r of dE/dG and a block of four columns, the
+      // four columns of every y_j read as one float4; each entry sums
+      // j = 0 .. S-1 in four partial sums (j mod 4, the tail into the first)
       const float* ry = per + L::oRY;
-      for (int e = lane; e < 6 * NV; e += S) {
-        const int r = e / NV, a = e % NV;
-        float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;  // independent partial sums
+      constexpr int NB = L::NVP / 4;
+      for (int task = lane; task < 6 * NB; task += S) {
+        const int r = task / NB, c0 = 4 * (task - r * NB);
+        float s[4][4];  // [column][partial sum]
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+#pragma unroll
+          for (int u = 0; u < 4; ++u) s[c][u] = 0.f;
+        auto acc = [&](int j, int u) {
+          const float rv = ry[j * L::RYW + r];
+          const float4 yv = *reinterpret_cast<const float4*>(ry + j * L::RYW + 8 + c0);
+          s[0][u] = fmaf(rv, yv.x, s[0][u]);
+          s[1][u] = fmaf(rv, yv.y, s[1][u]);
+          s[2][u] = fmaf(rv, yv.z, s[2][u]);
+          s[3][u] = fmaf(rv, yv.w, s[3][u]);
+        };
         int j = 0;
         for (; j + 3 < S; j += 4) {
-          s0 = fmaf(ry[j * (6 + NV) + r], ry[j * (6 + NV) + 6 + a], s0);
-          s1 = fmaf(ry[(j + 1) * (6 + NV) + r], ry[(j + 1) * (6 + NV) + 6 + a], s1);
-          s2 = fmaf(ry[(j + 2) * (6 + NV) + r], ry[(j + 2) * (6 + NV) + 6 + a], s2);
-          s3 = fmaf(ry[(j + 3) * (6 + NV) + r], ry[(j + 3) * (6 + NV) + 6 + a], s3);
+          acc(j, 0);
+          acc(j + 1, 1);
+          acc(j + 2, 2);
+          acc(j + 3, 3);
         }
-        for (; j < S; ++j) s0 = fmaf(ry[j * (6 + NV) + r], ry[j * (6 + NV) + 6 + a], s0);
-        per[L::oDG + e] = -2.f * A.w_q * ((s0 + s1) + (s2 + s3));
+        for (; j < S; ++j) acc(j, 0);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (c0 + c < NV) per[L::oDG + r * NV + c0 + c] = -2.f * A.w_q * ((s[c][0] + s[c][1]) + (s[c][2] + s[c][3]));
       }
       if (lane == 0) {
         float EQ = 0.f;

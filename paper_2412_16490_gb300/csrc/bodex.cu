@@ -227,8 +227,8 @@ __global__ void __launch_bounds__(RF_LANES * RF_GPB) refine_kernel(RefineArgs A)
       c[1] = dEdc[1];
       c[2] = dEdc[2];
       float s1, c1, s2, c2;
-      sincosf(xs[3], &s1, &c1);
-      sincosf(xs[4], &s2, &c2);
+      angle_sincos(xs[3], &s1, &c1);
+      angle_sincos(xs[4], &s2, &c2);
       const float om[3][3] = {{1.f, 0.f, 0.f}, {0.f, c1, s1}, {s2, -s1 * c2, c1 * c2}};
       const float rel[3] = {cf[0] - xs[0], cf[1] - xs[1], cf[2] - xs[2]};
       for (int k3 = 0; k3 < 3; ++k3) {

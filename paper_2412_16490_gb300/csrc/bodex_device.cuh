@@ -124,10 +124,23 @@ __device__ __forceinline__ void rot_vec(const float* R, const float* v, float* o
   o[2] = fmaf(R[6], v[0], fmaf(R[7], v[1], R[8] * v[2]));
 }
 
+// sin and cos of a joint or root angle: x is reduced to [-pi, pi] by
+// x - 2 pi k, k = rint(x / 2 pi), with 2 pi split into its float value and
+// the remainder (-1.748e-7), and the hardware approximation evaluates sin
+// and cos there (absolute error about 4e-7 on [-pi, pi]).  The clamp of
+// Eq. (4) keeps the angles within a few radians, where the reduction is
+// exact to float rounding.
+__device__ __forceinline__ void angle_sincos(float x, float* s, float* c) {
+  const float k = rintf(x * 0.159154943091895336f);
+  float r = fmaf(-k, 6.28318548202514648f, x);
+  r = fmaf(-k, -1.74845560007444870e-7f, r);
+  __sincosf(r, s, c);
+}
+
 // Rotation by q about the unit axis a (Rodrigues).
 __device__ __forceinline__ void rodrigues(const float* a, float q, float* R) {
   float s, c;
-  sincosf(q, &s, &c);
+  angle_sincos(q, &s, &c);
   const float C = 1.0f - c;
   R[0] = c + a[0] * a[0] * C;
   R[1] = a[0] * a[1] * C - a[2] * s;
@@ -144,9 +157,9 @@ __device__ __forceinline__ void rodrigues(const float* a, float q, float* R) {
 // virtual revolute joints (rx about world X, ry about Rx Y, rz about Rx Ry Z).
 __device__ __forceinline__ void root_frame(const float* x, Tf& T, float om[3][3]) {
   float s1, c1, s2, c2, s3, c3;
-  sincosf(x[3], &s1, &c1);
-  sincosf(x[4], &s2, &c2);
-  sincosf(x[5], &s3, &c3);
+  angle_sincos(x[3], &s1, &c1);
+  angle_sincos(x[4], &s2, &c2);
+  angle_sincos(x[5], &s3, &c3);
   T.R[0] = c2 * c3;
   T.R[1] = -c2 * s3;
   T.R[2] = s2;
@@ -326,7 +339,7 @@ __device__ inline SdfQ sdf_query(const ObjDev& O, const float* c) {
 // (JCGT 2017), sign taken from n_z.
 __device__ __forceinline__ void tangent_basis(const float* n, float* d, float* e) {
   const float sg = copysignf(1.0f, n[2]);
-  const float a = -1.0f / (sg + n[2]);
+  const float a = __fdividef(-1.0f, sg + n[2]);  // |sg + n_z| >= 1
   const float b = n[0] * n[1] * a;
   d[0] = 1.0f + sg * n[0] * n[0] * a;
   d[1] = sg * b;
@@ -354,9 +367,9 @@ struct ContactGeo {
 __device__ inline ContactGeo contact_geometry(const ObjDev& O, const float* c) {
   ContactGeo k;
   const SdfQ q = sdf_query(O, c);
-  const float L = sqrtf(q.g[0] * q.g[0] + q.g[1] * q.g[1] + q.g[2] * q.g[2]);
-  k.degenerate = !(L >= 1e-12f);
-  const float iL = 1.0f / L;
+  const float L2 = q.g[0] * q.g[0] + q.g[1] * q.g[1] + q.g[2] * q.g[2];
+  k.degenerate = !(L2 >= 1e-24f);
+  const float iL = rsqrtf(L2);
   const float gc[3] = {O.gcx, O.gcy, O.gcz};
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
@@ -1787,7 +1800,7 @@ __device__ inline void contact_adjoint(const ContactGeo& k, const float* dEdG_co
   // basis Jacobians (derivative of the Duff construction with the sign fixed)
   const float nx = k.n[0], ny = k.n[1], nz = k.n[2];
   const float sg = copysignf(1.0f, nz);
-  const float a = -1.0f / (sg + nz);
+  const float a = __fdividef(-1.0f, sg + nz);  // as in tangent_basis
   const float a2 = a * a;
   const float Jd[3][3] = {{2.f * sg * nx * a, 0.f, sg * nx * nx * a2},
                           {sg * ny * a, sg * nx * a, sg * nx * ny * a2},
@@ -1802,8 +1815,7 @@ __device__ inline void contact_adjoint(const ContactGeo& k, const float* dEdG_co
     dEdn[cc] = s;
   }
   // through p(c), n(c)
-  const float L = sqrtf(k.g[0] * k.g[0] + k.g[1] * k.g[1] + k.g[2] * k.g[2]);
-  const float iL = 1.0f / L;
+  const float iL = rsqrtf(k.g[0] * k.g[0] + k.g[1] * k.g[1] + k.g[2] * k.g[2]);  // as in contact_geometry
   const float no[3] = {k.g[0] * iL, k.g[1] * iL, k.g[2] * iL};
   const float Hs[3][3] = {{k.h[0], k.h[1], k.h[2]}, {k.h[1], k.h[3], k.h[4]}, {k.h[2], k.h[4], k.h[5]}};
   float Dno[3][3];  // (I - no no^T) Hs / L

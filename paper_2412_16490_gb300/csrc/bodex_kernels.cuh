@@ -1072,8 +1072,8 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
       // root rotations rx, ry, rz: axes through t
       {
         float s1, c1, s2, c2;
-        sincosf(xs[3], &s1, &c1);
-        sincosf(xs[4], &s2, &c2);
+        angle_sincos(xs[3], &s1, &c1);
+        angle_sincos(xs[4], &s2, &c2);
         const float om[3][3] = {{1.f, 0.f, 0.f}, {0.f, c1, s1}, {s2, -s1 * c2, c1 * c2}};
         const float rel[3] = {c[0] - xs[0], c[1] - xs[1], c[2] - xs[2]};
         for (int k3 = 0; k3 < 3; ++k3) {

@@ -619,7 +619,9 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
       R u1[7], u2[7];
       load_u_row(Us, j1, u1);
       load_u_row(Us, j2, u2);
-      for (int i = 0; i <= j2; ++i) {
+#pragma unroll
+      for (int i = 0; i < NV; ++i) {
+        if (i > j2) break;
         R ui[7];
         load_u_row(Us, i, ui);
         const R di = (i % 3 == 0) ? idn : idt;

@@ -1098,6 +1098,7 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
       // bias corrections 1 - b^t as 1 - 2^(t log2 b): a function of t alone,
       // so a run split over several launches gives the same values
       const float c1 = 1.f - exp2f((float)tstep * lb1), c2 = 1.f - exp2f((float)tstep * lb2);
+      const float ic1 = 1.f / c1, ic2 = 1.f / c2;  // once per step, not per coordinate
       for (int k = lane; k < D; k += S) {
         float g = 0.f;
         if (k < 6) {
@@ -1117,7 +1118,7 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
           ams[k] = mm;
           avs[k] = vv;
           const float lr = k < 3 ? A.lr_t : A.lr_r;
-          const float xn = xs[k] - lr * (mm / c1) / (sqrtf(vv / c2) + A.adam_eps);
+          const float xn = xs[k] - __fdividef(lr * (mm * ic1), sqrtf(vv * ic2) + A.adam_eps);
           xs[k] = fminf(fmaxf(xn, H.qmin[k]), H.qmax[k]);
         }
       }

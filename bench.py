@@ -37,7 +37,7 @@ FP32_LANES = 128  # FP32 FMA lanes per SM (Blackwell)
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused_kernel<5, step> launch on this
 # workload, from an ncu capture of a 5-step launch of the same kernel (the state is read once
 # per launch and the grid stays in L2, so the bytes do not grow with the steps)
-TRAFFIC_BYTES = 14_549_504 + 1_280
+TRAFFIC_BYTES = 14_556_160 + 2_816
 TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum of one fused_kernel<5, step> launch (5 steps)"
 
 
@@ -337,6 +337,7 @@ def run_ours(args, rank, world, local_rank):
     extra = {}
     if rank == 0 and not args.quick:
         extra["admm_sweep"] = admm_sweep(bx, torch, H, Ob, x_dev, T_dev, P, B)
+        extra["cta_sweep"] = cta_sweep(bx, torch, H, Ob, T_dev, P)
         extra["synthesis"] = synthesis_rate(bx, torch, H, Ob, x_dev, T_dev, sp)
         extra["energies"] = energy_variants(bx, torch, H, Ob, x_dev, T_dev, P)
         extra["exact_qps_200_steps"] = exact_run_rate(bx, torch, H, Ob, x_dev, T_dev, P)
@@ -573,6 +574,40 @@ def admm_sweep(bx, torch, H, Ob, x_dev, T_dev, P, B, steps=50, iters=(0, 25, 50,
     return {"upper_steps": steps, "ms_by_admm_iters": {str(k): out[k] for k in iters},
             "us_per_admm_iter": us_iter, "setup_us_per_upper_step": icpt / steps * 1e3,
             "admm_tflops": B * S * admm_iter_flops(H.m) / (us_iter * 1e-6) / 1e12}
+
+
+def cta_sweep(bx, torch, H, Ob, T_dev, P, steps=50, reps=4):
+    """ADMM rate of the fused step against the CTAs resident per SM: batches
+    of 1, 2, 3 and 4 CTAs (8 grasps each) per SM and the 4096-grasp batch,
+    each timed at 0 and 50 ADMM iterations (50 upper steps).  An SM's time
+    is set by its busiest warp scheduler, so the rate steps with the largest
+    count of warps on one scheduler rather than with the grasps."""
+    hand = I.hand_template("hand5")
+    obj = I.grid_object(2)
+    sms = sm_count()
+    out = {}
+    for B in (sms * 8, sms * 16, sms * 24, B_PER_GPU, sms * 32):
+        x_dev = torch.as_tensor(I.initial_poses(hand, obj, B, seed=2)).cuda()
+        st = bx.State(H, B, S)
+        ms = {}
+        for k in (0, 50):
+            sp = bx.step_params(P, qp=bx.qp_params(max_iter=k, eps_abs=0.0))
+            ts = []
+            for r in range(reps + 1):
+                st.set_pose(x_dev)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                bx.bodex_step(H, Ob, st, T_dev, steps, sp)
+                b.record()
+                torch.cuda.synchronize()
+                if r:
+                    ts.append(a.elapsed_time(b))
+            ms[k] = float(np.median(ts))
+        out[str(B)] = {"ctas_per_sm": B / 8 / sms, "ms_0_iters": ms[0], "ms_50_iters": ms[50],
+                       "qp_iterations_per_us": B * S * 50 * steps / ((ms[50] - ms[0]) * 1e3)}
+        del st
+    return {"upper_steps": steps, "grasps_per_cta": 8, "by_grasps": out}
 
 
 def synthesis_rate(bx, torch, H, Ob, x_dev, T_dev, sp, reps=2):

@@ -43,8 +43,9 @@ struct Lay {
   static constexpr int oG = 0;
   static constexpr int oK = align4(oG + 6 * NV);  // K^-1 setup scratch (16-byte aligned)
   static constexpr int oCT = oK + WoodburyScratch<M, double>::floats;
-  // per-lane record of the QP outputs: r_j (6), two pad words, then y_j
-  // from a 16-byte boundary (read as float4s by the dE/dG reduction)
+  // per-lane record of the QP outputs: r_j (6; read as a float4 and a
+  // float2 by the dE/dG reduction, so records start on 16-byte boundaries),
+  // two pad words, then y_j
   static constexpr int RYW = 8 + NVP;
   static constexpr int oRY = oCT + CTW * M;
   static constexpr int oQ = oRY + SMAX * RYW;
@@ -973,9 +974,10 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
       finish_qp();
     }
     __syncthreads();
-    // ---- A6: energy;  A7 (part 1): dE/dG = -2 w_Q sum_j r_j y_j^T
-    // (DFC: E_Q = |G u|^2 with u = 1 on every normal component, so
-    // dE/dG = 2 w_Q (G u) u^T: only the normal columns)
+    // ---- A6: energy;  A7 (part 1), DFC only: E_Q = |G u|^2 with u = 1 on
+    // every normal component, so dE/dG = 2 w_Q (G u) u^T (only the normal
+    // columns), written to shared memory.  The QP energy's
+    // dE/dG = -2 w_Q sum_j r_j y_j^T is formed per contact in part 2.
     if (active && A.dfc) {
       float gu[6];
 #pragma unroll
@@ -1007,26 +1009,50 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
         sc[0] = A.w_q * EQ + A.w_d * Ed + Ec;
       }
     }
-    if (active && !A.dfc) {
-      // a lane's task: row r of dE/dG and a block of four columns, the
-      // four columns of every y_j read as one float4; each entry sums
-      // j = 0 .. S-1 in four partial sums (j mod 4, the tail into the first)
-      const float* ry = per + L::oRY;
-      constexpr int NB = L::NVP / 4;
-      for (int task = lane; task < 6 * NB; task += S) {
-        const int r = task / NB, c0 = 4 * (task - r * NB);
-        float s[4][4];  // [column][partial sum]
+    if (active && !A.dfc && lane == 0) {
+      float EQ = 0.f;
+      for (int j = 0; j < S; ++j) EQ += per[L::oQ + j];
+      float Ed = 0.f;
+      for (int i = 0; i < M; ++i) {
+        const float r = per[L::oCT + L::CTW * i + 9] - H.alpha - A.delta;
+        Ed = fmaf(r, r, Ed);
+      }
+      float Ec = 0.f;
+      if (A.coll)
+        for (int l = 0; l < S; ++l) Ec += per[L::oGC + MAXD + l];
+      sc[0] = A.w_q * EQ + A.w_d * Ed + Ec;
+    }
+    // the QP energy's dE/dG is formed by the contact lanes below, from the
+    // r_j and y_j the QP lanes wrote before the last barrier; only DFC's
+    // shared dE/dG needs one more
+    if (A.dfc) __syncthreads();
+    // ---- A7 (part 2): through the contact geometry and the kinematic chain
+    if (active && lane < M) {
+      const ContactGeo k = load_ct(per + L::oCT + L::CTW * lane);
+      float cols[18];
+      if (A.dfc) {
+        for (int r = 0; r < 6; ++r)
+          for (int cc = 0; cc < 3; ++cc) cols[r * 3 + cc] = per[L::oDG + r * NV + 3 * lane + cc];
+      } else {
+        // this contact's three columns of dE/dG = -2 w_Q sum_j r_j y_j^T,
+        // each entry summing j in four partial sums (j mod 4, the tail
+        // into the first)
+        const float* ry = per + L::oRY;
+        float s[18][4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
+        for (int e = 0; e < 18; ++e)
 #pragma unroll
-          for (int u = 0; u < 4; ++u) s[c][u] = 0.f;
+          for (int u = 0; u < 4; ++u) s[e][u] = 0.f;
         auto acc = [&](int j, int u) {
-          const float rv = ry[j * L::RYW + r];
-          const float4 yv = *reinterpret_cast<const float4*>(ry + j * L::RYW + 8 + c0);
-          s[0][u] = fmaf(rv, yv.x, s[0][u]);
-          s[1][u] = fmaf(rv, yv.y, s[1][u]);
-          s[2][u] = fmaf(rv, yv.z, s[2][u]);
-          s[3][u] = fmaf(rv, yv.w, s[3][u]);
+          const float4 r03 = *reinterpret_cast<const float4*>(ry + j * L::RYW);
+          const float2 r45 = *reinterpret_cast<const float2*>(ry + j * L::RYW + 4);
+          const float rv[6] = {r03.x, r03.y, r03.z, r03.w, r45.x, r45.y};
+          const float* yj = ry + j * L::RYW + 8 + 3 * lane;
+          const float yv[3] = {yj[0], yj[1], yj[2]};
+#pragma unroll
+          for (int r = 0; r < 6; ++r)
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) s[r * 3 + cc][u] = fmaf(rv[r], yv[cc], s[r * 3 + cc][u]);
         };
         int j = 0;
         for (; j + 3 < S; j += 4) {
@@ -1037,30 +1063,8 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
         }
         for (; j < S; ++j) acc(j, 0);
 #pragma unroll
-        for (int c = 0; c < 4; ++c)
-          if (c0 + c < NV) per[L::oDG + r * NV + c0 + c] = -2.f * A.w_q * ((s[c][0] + s[c][1]) + (s[c][2] + s[c][3]));
+        for (int e = 0; e < 18; ++e) cols[e] = -2.f * A.w_q * ((s[e][0] + s[e][1]) + (s[e][2] + s[e][3]));
       }
-      if (lane == 0) {
-        float EQ = 0.f;
-        for (int j = 0; j < S; ++j) EQ += per[L::oQ + j];
-        float Ed = 0.f;
-        for (int i = 0; i < M; ++i) {
-          const float r = per[L::oCT + L::CTW * i + 9] - H.alpha - A.delta;
-          Ed = fmaf(r, r, Ed);
-        }
-        float Ec = 0.f;
-        if (A.coll)
-          for (int l = 0; l < S; ++l) Ec += per[L::oGC + MAXD + l];
-        sc[0] = A.w_q * EQ + A.w_d * Ed + Ec;
-      }
-    }
-    __syncthreads();
-    // ---- A7 (part 2): through the contact geometry and the kinematic chain
-    if (active && lane < M) {
-      const ContactGeo k = load_ct(per + L::oCT + L::CTW * lane);
-      float cols[18];
-      for (int r = 0; r < 6; ++r)
-        for (int cc = 0; cc < 3; ++cc) cols[r * 3 + cc] = per[L::oDG + r * NV + 3 * lane + cc];
       float dEdc[3];
       contact_adjoint(k, cols, 2.f * A.w_d * (k.phi - H.alpha - A.delta), dEdc);
       const float* jw = per + L::oJW + lane * MAXCHAIN * 6;  // frames from the forward pass

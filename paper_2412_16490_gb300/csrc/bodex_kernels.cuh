@@ -113,11 +113,11 @@ __device__ __forceinline__ bool finite3(const float* v) {
 // Double precision when the host asks for it (solves that iterate to a
 // tight residual target), single precision otherwise; the branch is
 // uniform per launch.
-template <int M>
+template <int M, bool UNROLL = false>
 __device__ inline void setup_kinv(bool active, int lane, int S, const float* Gs, float* scratch, float* Kinv,
                                   const AdmmCfg& cfg) {
   if (cfg.fp64_setup) setup_kinv_woodbury<M, double>(active, lane, S, Gs, scratch, Kinv, cfg);
-  else setup_kinv_woodbury<M, float>(active, lane, S, Gs, scratch, Kinv, cfg);
+  else setup_kinv_woodbury<M, float, UNROLL>(active, lane, S, Gs, scratch, Kinv, cfg);
 }
 
 // ============================================================================ kernel: batched QP
@@ -848,9 +848,9 @@ __device__ __forceinline__ void fused_cta(const FusedArgs& A, int cta, int GPB, 
       if constexpr (ADAPT) {
         AdmmCfg cg = cfg;
         cg.rho = sc[3];
-        setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cg);
+        setup_kinv<M, true>(active, lane, S, Gs, per + L::oK, kin, cg);
       } else {
-        setup_kinv<M>(active, lane, S, Gs, per + L::oK, kin, cfg);
+        setup_kinv<M, true>(active, lane, S, Gs, per + L::oK, kin, cfg);
       }
     }
     // ---- A5: ADMM, one QP per lane

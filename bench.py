@@ -37,7 +37,7 @@ FP32_LANES = 128  # FP32 FMA lanes per SM (Blackwell)
 # dram__bytes_read.sum + dram__bytes_write.sum of one fused_kernel<5, step> launch on this
 # workload, from an ncu capture of a 5-step launch of the same kernel (the state is read once
 # per launch and the grid stays in L2, so the bytes do not grow with the steps)
-TRAFFIC_BYTES = 14_556_928 + 2_816
+TRAFFIC_BYTES = 14_563_072 + 4_864
 TRAFFIC_SOURCE = "ncu dram__bytes_read.sum + dram__bytes_write.sum of one fused_kernel<5, step> launch (5 steps)"
 
 

@@ -276,6 +276,15 @@ def run_ours(args, rank, world, local_rank):
         if rank == 0:
             print(json.dumps({"workload": f"paper workload, {n_up} upper steps with exact QPs", "launches": 2}))
         return
+    if args.setup_only:  # the fused step's set-up phases alone (a small command for profiler captures)
+        sp_0 = bx.step_params(P, qp=bx.qp_params(max_iter=0, eps_abs=0.0))
+        for _ in range(2):
+            st.set_pose(x_dev)
+            bx.bodex_step(H, Ob, st, T_dev, n_up, sp_0, E_last=E_dev, status=stat_dev)
+        torch.cuda.synchronize()
+        if rank == 0:
+            print(json.dumps({"workload": f"paper workload, {n_up} upper steps at 0 ADMM iterations", "launches": 2}))
+        return
     if args.qp_exact_only:  # the exact QP solver alone (a small command for profiler captures)
         line = qp_exact_rate(bx, torch, H, Ob, x_dev, T_dev)
         if rank == 0:
@@ -908,6 +917,9 @@ def main():
     ap.add_argument("--qp-only", action="store_true", help="only the standalone QP measurement (profiler captures)")
     ap.add_argument("--exact-step-only", action="store_true",
                     help="only two fused runs with exact QPs (profiler captures; --upper-steps sets their length)")
+    ap.add_argument("--setup-only", action="store_true",
+                    help="only two fused runs at 0 ADMM iterations, i.e. the per-step set-up alone "
+                         "(profiler captures; --upper-steps sets their length)")
     ap.add_argument("--qp-exact-only", action="store_true",
                     help="only the exact-solver QP measurement (profiler captures)")
     ap.add_argument("--mixed-only", action="store_true",

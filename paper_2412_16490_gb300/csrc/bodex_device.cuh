@@ -129,7 +129,7 @@ __device__ __forceinline__ void rot_vec(const float* R, const float* v, float* o
 // the remainder (-1.748e-7), and the hardware approximation evaluates sin
 // and cos there (absolute error about 4e-7 on [-pi, pi]).  The clamp of
 // Eq. (4) keeps the angles within a few radians, where the reduction is
-// exact to float rounding.
+// accurate to float rounding.
 __device__ __forceinline__ void angle_sincos(float x, float* s, float* c) {
   const float k = rintf(x * 0.159154943091895336f);
   float r = fmaf(-k, 6.28318548202514648f, x);
@@ -642,8 +642,8 @@ __device__ inline void setup_kinv_woodbury(bool active, int lane, int S, const f
   __syncthreads();
   // alpha K^-1 = alpha (Dg^-1 - U U^T), entry (i, j) of the upper triangle
   // at Admm<M>::tri(i, j).  Lane p takes the columns j1 = p and
-  // j2 = nv-1-p (nv + 1 entries between them, so the lanes' shares are
-  // equal), holds their rows of U in registers and walks i = 0 .. j2 in step
+  // j2 = nv-1-p (nv + 1 entries between them; the middle column alone for
+  // odd nv), holds their rows of U in registers and walks i = 0 .. j2 in step
   // with the grasp's other lanes: at each i they all read the same row of U,
   // one broadcast load, where spreading single entries over the lanes had
   // each lane read two rows of its own per entry.

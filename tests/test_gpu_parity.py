@@ -115,7 +115,7 @@ def qp_bar(Q_ref):
 
 
 @pytest.mark.parametrize("wl,B", [("tiny", 64), ("paper_small", 96), ("paper_near", 64)])
-def test_qp_value_north_star_bar(wl, B, request):
+def test_qp_value_within_1e4_relative(wl, B, request):
     """The unregularised QPs of Eqs. (7)-(9) at G from the oracle: ADMM to a
     1e-6 residual (K^-1 built in FP64), every QP converged, then polished
     (the exact minimum-norm-point solve in FP64): every QP's value within
@@ -149,7 +149,7 @@ def test_qp_value_north_star_bar(wl, B, request):
 
 
 @pytest.mark.parametrize("wl,B", [("tiny", 64), ("paper_small", 96), ("paper_near", 64)])
-def test_qp_exact_solver_north_star_bar(wl, B, request):
+def test_qp_exact_solver_value_within_1e4_relative(wl, B, request):
     """qp.solver = EXACT (the float32 minimum-norm-point method, no ADMM):
     no QP stopped by the oracle-call cap; every QP's value within
     1e-4 |Q*| + 1e-6 of the oracle's; the Frank-Wolfe gap reported in

@@ -159,11 +159,12 @@ def paper_sample_size(budget_s: float, threads: int, cap: int = 256) -> int:
 
 
 def cpu_baseline(budget_s: float):
-    """The oracle on the host cores: the paper workload (config 2) as one
-    measured 200-step run of up to 256 grasps; the tiny workload (config 1)
-    in full, 64 grasps x 50 steps; the differentiation workload (config 3)
-    in full: the evaluation of its 1024 grasps plus central differences
-    (h = 1e-6) on its 64 sampled instances; and config 2 on one core."""
+    """The oracle on the host cores: the paper-scale workload (4096 grasps,
+    5-finger hand) as one measured 200-step run of up to 256 of its grasps;
+    the tiny workload in full, 64 grasps x 50 steps; the differentiation
+    workload in full: the evaluation of its 1024 grasps plus central
+    differences (h = 1e-6) on its 64 sampled instances; and the paper-scale
+    workload on one core."""
     import oracle as O
     th = O.default_threads()
     g = paper_sample_size(budget_s, th)
